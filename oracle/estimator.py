@@ -1,0 +1,137 @@
+"""Algorithm 1 (the r_k log-determinant estimator) and exact log det.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Section 2 writes log det M = log det P + tr log(M P^-1) and replaces log by the
+partial-fraction form of r_k (Table 1), then estimates the trace with
+Hutchinson's estimator over s probe vectors (Section 1; the "(1/n) sum over n"
+printed there is read as (1/s) sum over the s probes, as in Algorithm 1's
+output).  Algorithm 1 obtains each shifted quadratic form from t Lanczos
+steps and a tridiagonal (Thomas) solve per shift.
+
+Readings (where the paper is silent or garbled):
+
+* Lanczos runs on the symmetric B = L^-1 M L^-T (``precond.operator_B``),
+  which is similar to M P^-1 and so has the same trace of r_k;
+* one Krylov space per probe; Algorithm 1's "(T - alpha_i)" and "Q^t w_j" are
+  read as (T - alpha_j) with alpha_j = -sigma_j and Q^t w_{i,j};
+* ``estimate_lanczos`` is Algorithm 1 taken literally (t steps, full
+  reorthogonalisation, Thomas); ``estimate_converged`` is its t -> infinity
+  limit, z^T (B + sigma_j I)^-1 z by a Cholesky solve.
+"""
+import numpy as np
+
+from . import coeffs
+
+
+def logdet_exact(M):
+    """log det M = 2 sum log diag(chol(M)) (Section 3's ground truth)."""
+    L = np.linalg.cholesky(np.asarray(M, dtype=np.float64))
+    return 2.0 * float(np.sum(np.log(np.diag(L))))
+
+
+def shifted_quadforms(B, Z, sigma):
+    """q[i, j] = z_i^T (B + sigma_j I)^-1 z_i by Cholesky solves (n-by-s Z)."""
+    n = B.shape[0]
+    q = np.empty((Z.shape[1], len(sigma)))
+    for j, sj in enumerate(sigma):
+        L = np.linalg.cholesky(B + sj * np.eye(n))
+        Y = np.linalg.solve(L, Z)  # L^-1 Z
+        q[:, j] = np.einsum("ij,ij->j", Y, Y)
+    return q
+
+
+def combine(logdet_P, Z, q, k):
+    """Algorithm 1 output: log det P + (1/s) sum_i [b |z_i|^2 + sum_j c_j q_ij].
+
+    Returns (estimate, per-probe values of the bracket).
+    """
+    b, c, _ = coeffs.rk_coeffs(k)
+    znorm2 = np.einsum("ij,ij->j", Z, Z)
+    per_probe = b * znorm2 + q @ c
+    return float(logdet_P + np.mean(per_probe)), per_probe
+
+
+def estimate_converged(B, logdet_P, Z, k):
+    """Estimator with exact shifted solves (Algorithm 1 with t -> infinity)."""
+    _, _, sigma = coeffs.rk_coeffs(k)
+    q = shifted_quadforms(B, np.asarray(Z, dtype=np.float64), sigma)
+    est, per_probe = combine(logdet_P, Z, q, k)
+    return est, per_probe, q
+
+
+def lanczos(B, v, t):
+    """t steps of Lanczos on symmetric B from v/|v| with full reorthogonalisation.
+
+    Returns the tridiagonal T as (diag, offdiag) and the t-by-n basis Q (rows).
+    Stops early on an invariant subspace (beta = 0).
+    """
+    n = B.shape[0]
+    Q = np.zeros((t, n))
+    alpha = np.zeros(t)
+    beta = np.zeros(t)
+    q = v / np.linalg.norm(v)
+    m = t
+    for k in range(t):
+        Q[k] = q
+        w = B @ q
+        alpha[k] = q @ w
+        w = w - Q[:k + 1].T @ (Q[:k + 1] @ w)
+        w = w - Q[:k + 1].T @ (Q[:k + 1] @ w)
+        beta[k] = np.linalg.norm(w)
+        if k + 1 == t:
+            break
+        if beta[k] <= 1e-14 * max(1.0, abs(alpha[k])):
+            m = k + 1
+            break
+        q = w / beta[k]
+    return alpha[:m], beta[:m - 1], Q[:m]
+
+
+def thomas(lower, diag, upper, rhs):
+    """Thomas algorithm for a tridiagonal system (Section 2 cites Thomas 1949)."""
+    m = len(diag)
+    cp = np.zeros(m)
+    dp = np.zeros(m)
+    cp[0] = upper[0] / diag[0] if m > 1 else 0.0
+    dp[0] = rhs[0] / diag[0]
+    for i in range(1, m):
+        den = diag[i] - lower[i - 1] * cp[i - 1]
+        cp[i] = upper[i] / den if i < m - 1 else 0.0
+        dp[i] = (rhs[i] - lower[i - 1] * dp[i - 1]) / den
+    x = np.zeros(m)
+    x[-1] = dp[-1]
+    for i in range(m - 2, -1, -1):
+        x[i] = dp[i] - cp[i] * x[i + 1]
+    return x
+
+
+def estimate_lanczos(B, logdet_P, Z, k, t):
+    """Algorithm 1 taken literally: Lanczos (t steps) then Thomas per shift."""
+    _, _, sigma = coeffs.rk_coeffs(k)
+    Z = np.asarray(Z, dtype=np.float64)
+    s = Z.shape[1]
+    q = np.empty((s, len(sigma)))
+    for i in range(s):
+        v = Z[:, i]
+        vn = np.linalg.norm(v)
+        a, bt, _ = lanczos(B, v, t)
+        m = len(a)
+        e1 = np.zeros(m)
+        e1[0] = vn
+        for j, sj in enumerate(sigma):
+            w = thomas(bt, a + sj, bt, e1)  # (T - alpha_j) w = |v| e_1
+            q[i, j] = vn * w[0]             # v^T Q^T w = |v| e_1^T w
+    est, per_probe = combine(logdet_P, Z, q, k)
+    return est, per_probe, q
+
+
+def rk_bias(B, k):
+    """Exact r_k bias of the trace term: sum_i [log lam_i(B) - r_k(lam_i(B))]."""
+    lam = np.linalg.eigvalsh(B)
+    return float(np.sum(np.log(lam) - coeffs.rk_eval_pf(k, lam)))
+
+
+def trace_rk(B, k):
+    """tr r_k(B) = sum_i r_k(lam_i(B)) from the eigenvalues."""
+    return float(np.sum(coeffs.rk_eval_pf(k, np.linalg.eigvalsh(B))))

@@ -1,0 +1,120 @@
+"""Pins for oracle/estimator.py: Hutchinson exactness, M = P, exhaustive probes,
+Lanczos = direct solves, Cholesky log det, bias formula."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import coeffs, estimator, kernels, precond
+from oracle.splitmix import rademacher_block
+from paper_2405_03474_gb300 import inputs
+
+
+def test_logdet_exact_against_lu_and_diagonal():
+    X = inputs.points(250, 3, "normal", seed=1)
+    M = kernels.kernel_matrix(X, kernels.RBF, 0.7, 1.0, 1e-2)
+    sign, ref = np.linalg.slogdet(M)  # LU, an independent factorisation
+    assert sign > 0
+    assert estimator.logdet_exact(M) == pytest.approx(ref, rel=1e-12)
+    d = np.array([0.5, 2.0, 3.0, 7.0])
+    assert estimator.logdet_exact(np.diag(d)) == pytest.approx(np.sum(np.log(d)), rel=1e-15)
+    # 2x2 closed form
+    M2 = np.array([[2.0, 0.5], [0.5, 1.0]])
+    assert estimator.logdet_exact(M2) == pytest.approx(np.log(2.0 - 0.25), rel=1e-15)
+
+
+@pytest.mark.parametrize("k", coeffs.ORDERS)
+def test_hutchinson_exact_on_diagonal(k):
+    # M diagonal, P = I: z^T r(M) z = sum_i z_i^2 r(m_ii) = sum_i r(m_ii) for every sign z.
+    d = np.random.default_rng(3).uniform(0.1, 5.0, 64)
+    M = np.diag(d)
+    Z = rademacher_block(5, 64, 6)
+    est, per_probe, _ = estimator.estimate_converged(M, 0.0, Z, k)
+    ref = float(np.sum(coeffs.rk_eval_pf(k, d)))
+    np.testing.assert_allclose(per_probe, ref, rtol=1e-13)
+    assert est == pytest.approx(ref, rel=1e-13)
+
+
+@pytest.mark.parametrize("k", coeffs.ORDERS)
+def test_M_equal_P_gives_logdet_P(k):
+    # B = I, r(1) = 0: the estimate is log det P for every probe.
+    rng = np.random.default_rng(4)
+    n, r = 90, 5
+    A = rng.standard_normal((n, r))
+    D = rng.uniform(0.5, 2.0, n)
+    M = np.diag(D) + A @ A.T
+    F = precond.factors(A, D)
+    B = precond.operator_B(M, F)
+    np.testing.assert_allclose(B, np.eye(n), atol=1e-12)
+    est, per_probe, _ = estimator.estimate_converged(B, F["logdet_P"], rademacher_block(1, n, 4), k)
+    np.testing.assert_allclose(per_probe, 0.0, atol=1e-10)
+    assert est == pytest.approx(np.linalg.slogdet(M)[1], rel=1e-12)
+
+
+@pytest.mark.parametrize("k", coeffs.ORDERS)
+def test_exhaustive_probes_give_trace_of_rk(k):
+    # Averaging z^T r(B) z over all 2^n sign vectors gives tr r(B) = sum r(lam_i(B)).
+    n = 8
+    X = inputs.points(n, 2, "uniform", seed=7)
+    M = kernels.kernel_matrix(X, kernels.MATERN52, 0.4, 1.0, 0.05)
+    A, D = precond.build(M, rademacher_block(2, n, 2), 1, 0.05)
+    F = precond.factors(A, D)
+    B = precond.operator_B(M, F)
+    Z = np.array(list(itertools.product([-1.0, 1.0], repeat=n))).T
+    est, _, _ = estimator.estimate_converged(B, F["logdet_P"], Z, k)
+    assert est == pytest.approx(F["logdet_P"] + estimator.trace_rk(B, k), rel=1e-12)
+    # and log det M minus that equals the exact r_k bias
+    assert estimator.logdet_exact(M) - est == pytest.approx(estimator.rk_bias(B, k), abs=1e-10)
+
+
+def test_thomas_matches_dense_solve():
+    rng = np.random.default_rng(8)
+    m = 12
+    diag = rng.uniform(3, 4, m)
+    off = rng.uniform(-1, 1, m - 1)
+    rhs = rng.standard_normal(m)
+    T = np.diag(diag) + np.diag(off, 1) + np.diag(off, -1)
+    np.testing.assert_allclose(estimator.thomas(off, diag, off, rhs), np.linalg.solve(T, rhs), rtol=1e-12)
+
+
+def test_lanczos_reproduces_B_and_full_t_equals_direct():
+    n = 60
+    X = inputs.points(n, 2, "uniform", seed=9)
+    M = kernels.kernel_matrix(X, kernels.RBF, 0.3, 1.0, 1e-1)
+    F = precond.factors(*precond.identity(n))
+    B = precond.operator_B(M, F)
+    v = rademacher_block(3, n, 1)[:, 0]
+    a, bt, Q = estimator.lanczos(B, v, 10)
+    T = np.diag(a) + np.diag(bt, 1) + np.diag(bt, -1)
+    np.testing.assert_allclose(Q @ Q.T, np.eye(len(a)), atol=1e-12)
+    np.testing.assert_allclose(Q @ B @ Q.T, T, atol=1e-10)
+    Z = rademacher_block(4, n, 3)
+    for k in coeffs.ORDERS:
+        e1, p1, _ = estimator.estimate_lanczos(B, 0.0, Z, k, n)
+        e2, p2, _ = estimator.estimate_converged(B, 0.0, Z, k)
+        np.testing.assert_allclose(p1, p2, rtol=1e-9)
+
+
+def test_lanczos_quadrature_converges_with_t():
+    n = 200
+    X = inputs.points(n, 2, "uniform", seed=10)
+    M = kernels.kernel_matrix(X, kernels.MATERN52, 0.2, 1.0, 1e-2)
+    A, D = precond.build(M, rademacher_block(2, n, 16), 3, 1e-2)
+    F = precond.factors(A, D)
+    B = precond.operator_B(M, F)
+    Z = rademacher_block(1, n, 4)
+    ref, _, _ = estimator.estimate_converged(B, F["logdet_P"], Z, 3)
+    errs = [abs(estimator.estimate_lanczos(B, F["logdet_P"], Z, 3, t)[0] - ref) for t in (2, 5, 10, 40)]
+    assert errs[-1] < 1e-8 * abs(ref)
+    assert errs[0] > errs[2]
+
+
+def test_r3_more_accurate_than_r1_on_kernel_matrices():
+    # Section 3: r_3 has lower error than r_1 (here: the exact r_k bias, no probe noise).
+    for kind in (kernels.RBF, kernels.MATERN52):
+        X = inputs.points(300, 5, "normal", seed=11)
+        M = kernels.kernel_matrix(X, kind, 1.0, 1.0, 1e-2)
+        A, D = precond.build(M, rademacher_block(2, 300, 25), 5, 1e-2)
+        B = precond.operator_B(M, precond.factors(A, D))
+        b1, b3, b5 = (abs(estimator.rk_bias(B, k)) for k in (1, 3, 5))
+        assert b3 < b1 and b5 < b1
