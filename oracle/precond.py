@@ -16,14 +16,15 @@ SVD").  Readings taken where the paper is silent:
   A = Q V Lambda^(1/2);
 * D = diag(M) - rowsumsq(A), clamped below at max(nu, 1e-12 * diag(M)).
 
-The symmetric split factor used by the estimator (P = L L^T) is
+The split factor used by the estimator (P = L L^T; the paper runs Lanczos on
+M P^-1 and leaves the factor open) is built from the thin QR of G = D^-1/2 A:
 
-    G = D^-1/2 A,   L = D^1/2 (I + G G^T)^1/2,
-    L^-1 = (I + G E G^T) D^-1/2,   E = f(G^T G),
-    f(lam) = ((1 + lam)^-1/2 - 1) / lam = -1 / (sqrt(1+lam) (1 + sqrt(1+lam))),
+    G = Q_G R_G   (Householder, diag(R_G) > 0),
+    C C^T = I + R_G R_G^T   (Cholesky, C lower triangular),
+    R = I + Q_G (C - I) Q_G^T,  so  R R^T = I + G G^T,
+    L = D^1/2 R,   L^-1 = (I + Q_G (C^-1 - I) Q_G^T) D^-1/2,
 
-so that (I + G G^T)^-1/2 = I + G E G^T exactly, and by the matrix
-determinant lemma log det P = sum log D + log det(I + G^T G).
+and by the matrix determinant lemma log det P = sum log D + 2 sum log C_kk.
 """
 import numpy as np
 
@@ -69,43 +70,47 @@ def build(M, Omega, q, noise):
 
 
 def factors(A, D):
-    """Symmetric split factor of P = D + A A^T.
+    """Split factor of P = D + A A^T (see module docstring).
 
-    Returns dict with G (n-by-r), E (r-by-r), dinv_sqrt (n) and logdet_P.
+    Returns dict with Q (n-by-r), Cinv (r-by-r lower), dinv_sqrt (n), logdet_P.
     """
     A = np.asarray(A, dtype=np.float64)
     D = np.asarray(D, dtype=np.float64)
     n, r = A.shape
     dinv_sqrt = 1.0 / np.sqrt(D)
     G = A * dinv_sqrt[:, None]
-    H = G.T @ G
     if r > 0:
-        lam, W = np.linalg.eigh(0.5 * (H + H.T))
-        lam = np.maximum(lam, 0.0)
-        sq = np.sqrt(1.0 + lam)
-        E = (W * (-1.0 / (sq * (1.0 + sq)))[None, :]) @ W.T
-        core = np.linalg.cholesky(np.eye(r) + H)
-        logdet_core = 2.0 * np.sum(np.log(np.diag(core)))
+        Q, RG = np.linalg.qr(G)
+        sgn = np.sign(np.diag(RG))
+        sgn[sgn == 0] = 1.0
+        Q = Q * sgn[None, :]
+        RG = RG * sgn[:, None]
+        C = np.linalg.cholesky(np.eye(r) + RG @ RG.T)
+        Cinv = np.linalg.inv(C)
+        logdet_core = 2.0 * np.sum(np.log(np.diag(C)))
     else:
-        E = np.zeros((0, 0))
+        Q = np.zeros((n, 0))
+        Cinv = np.zeros((0, 0))
         logdet_core = 0.0
     return {
-        "G": G,
-        "E": E,
+        "Q": Q,
+        "Cinv": Cinv,
         "dinv_sqrt": dinv_sqrt,
         "logdet_P": float(np.sum(np.log(D)) + logdet_core),
     }
 
 
 def apply_Linv(F, V):
-    """L^-1 V = (I + G E G^T) D^-1/2 V."""
+    """L^-1 V = (I + Q (C^-1 - I) Q^T) D^-1/2 V."""
     W = F["dinv_sqrt"][:, None] * V
-    return W + F["G"] @ (F["E"] @ (F["G"].T @ W))
+    T = F["Q"].T @ W
+    return W + F["Q"] @ (F["Cinv"] @ T - T)
 
 
 def apply_LinvT(F, V):
-    """L^-T V = D^-1/2 (I + G E G^T) V."""
-    W = V + F["G"] @ (F["E"] @ (F["G"].T @ V))
+    """L^-T V = D^-1/2 (I + Q (C^-T - I) Q^T) V."""
+    T = F["Q"].T @ V
+    W = V + F["Q"] @ (F["Cinv"].T @ T - T)
     return F["dinv_sqrt"][:, None] * W
 
 

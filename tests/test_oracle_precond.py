@@ -23,16 +23,19 @@ def test_logdet_P_matches_dense_slogdet():
 
 
 def test_split_factor_inverts_P():
-    # L^-1 P L^-T = I, and R^-1 = I + G E G^T is the inverse square root of I + G G^T.
+    # L^-1 P L^-T = I, Q is orthonormal, and R = I + Q (C - I) Q^T has R R^T = I + G G^T.
     A, D = _random_lowrank(150, 9, 1)
     F = precond.factors(A, D)
     P = np.diag(D) + A @ A.T
     Li = precond.dense_Linv(F)
     np.testing.assert_allclose(Li @ P @ Li.T, np.eye(150), atol=1e-11)
-    G = F["G"]
-    Rinv = np.eye(150) + G @ F["E"] @ G.T
-    np.testing.assert_allclose(Rinv, Rinv.T, atol=1e-14)
-    np.testing.assert_allclose(Rinv @ (np.eye(150) + G @ G.T) @ Rinv, np.eye(150), atol=1e-11)
+    Q = F["Q"]
+    np.testing.assert_allclose(Q.T @ Q, np.eye(9), atol=1e-13)
+    C = np.linalg.inv(F["Cinv"])
+    assert np.allclose(np.triu(C, 1), 0.0)
+    R = np.eye(150) + Q @ (C - np.eye(9)) @ Q.T
+    G = A / np.sqrt(D)[:, None]
+    np.testing.assert_allclose(R @ R.T, np.eye(150) + G @ G.T, atol=1e-11)
     V = np.random.default_rng(2).standard_normal((150, 4))
     np.testing.assert_allclose(precond.apply_LinvT(F, V), Li.T @ V, atol=1e-12)
 
