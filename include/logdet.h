@@ -1,0 +1,240 @@
+/*
+ * logdet.h -- C ABI of liblogdet.so, a GB300 (sm_103a) implementation of the
+ * rational-function log-determinant estimator of Colthurst, Vasudevan, Lottes
+ * and Patton, "Fast Approximate Determinants Using Rational Functions"
+ * (arXiv 2405.03474):
+ *
+ *     log det M  =  log det P + tr log(M P^-1)
+ *               ~=  log det P + (1/s) sum_i z_i^T r_k(B) z_i ,
+ *
+ * with r_k (k = 1, 3, 5) from Eq. 1 in the partial-fraction form of Table 1,
+ * Rademacher probes z_i (Section 2, Algorithm 1 step 1), B = L^-1 M L^-T
+ * (similar to M P^-1; P = L L^T) and P a randomized truncated-SVD
+ * preconditioner (Section 2; Appendix "Truncated Randomized SVD").
+ *
+ * Conventions for every entry point:
+ *   - Every block of vectors is ROW-MAJOR n-by-c: element (i, j) at [i*c + j].
+ *     X is n-by-d points (float64), probes are n-by-s int8 (+1/-1).
+ *   - Pointers named *_dev are device memory, *_host host memory.  The caller
+ *     owns all of them; the library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; calls that return host scalars
+ *     (ld_result, logdet_P, grad) synchronise that stream before returning.
+ *   - `ws`/`ws_bytes`: caller-provided device scratch.  Pass ws = NULL to let
+ *     the library cudaMalloc (and free before returning) what it needs;
+ *     otherwise ws_bytes must be >= the size the matching *_workspace_size
+ *     query returns, else LD_ERR_WORKSPACE.
+ *   - Return value: LD_OK (0) or a negative ld_status.  On error nothing is
+ *     left allocated; ld_last_error() gives a one-line reason.
+ *   - Handles (ld_precond, ld_surrogate) own device memory and are freed with
+ *     their *_free function.
+ *   - One device: the current CUDA device of the calling thread.
+ */
+#ifndef LOGDET_H
+#define LOGDET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+typedef enum {
+    LD_OK = 0,
+    LD_ERR_INVALID = -1,        /* bad argument (size, pointer, option)          */
+    LD_ERR_NOT_SPD = -2,        /* a Cholesky pivot <= 0 (matrix not SPD)         */
+    LD_ERR_NOT_CONVERGED = -3,  /* CG hit max_iters before rel_tol; out is filled */
+    LD_ERR_CUDA = -4,           /* a CUDA runtime call failed                     */
+    LD_ERR_WORKSPACE = -5,      /* ws_bytes smaller than required                 */
+    LD_ERR_UNSUPPORTED = -6,    /* option combination not built                   */
+    LD_ERR_DEVICE_TIMEOUT = -7  /* a device-side wait gave up (bounded spin)      */
+} ld_status;
+
+/* Kernel families of Section 3 (forms of Rasmussen & Williams):
+ *   RBF:        k(r) = v exp(-r^2 / (2 l^2))
+ *   MATERN52:   k(r) = v (1 + u + u^2/3) exp(-u),  u = sqrt(5) r / l
+ * M = K + noise * I. */
+typedef enum { LD_RBF = 0, LD_MATERN52 = 1 } ld_kernel_kind;
+
+/* Arithmetic of the kernel product K V (the O(n^2) step of Algorithm 1):
+ *   LD_FP64      SIMT float64 everywhere (parity mode)
+ *   LD_FP32      SIMT float32 kernel values and products
+ *   LD_BF16_TC   tensor cores (tcgen05), K and V rounded to bf16, fp32 accumulate
+ *   LD_F16_TC    tensor cores, K and V rounded to fp16 (V scaled per column)
+ *   LD_F16X3_TC  tensor cores, hi/lo fp16 split of K and V, 3 products
+ *                (K_hi V_hi + K_hi V_lo + K_lo V_hi), fp32 accumulate
+ * Non-FP64 modes keep CG vectors in fp32 and every reduction in fp64. */
+typedef enum {
+    LD_FP64 = 0,
+    LD_FP32 = 1,
+    LD_BF16_TC = 2,
+    LD_F16_TC = 3,
+    LD_F16X3_TC = 4
+} ld_precision;
+
+typedef struct {
+    int32_t kind;        /* ld_kernel_kind */
+    int32_t reserved;
+    double lengthscale;  /* l > 0 */
+    double variance;     /* v > 0 */
+    double noise;        /* nu >= 0, added to the diagonal */
+} ld_kernel;
+
+typedef struct {
+    int32_t order;           /* k of r_k: 1, 3 or 5 (Eq. 1, Table 1) */
+    int32_t num_probes;      /* s, total probes (Algorithm 1 input s) */
+    int32_t probes_per_block;/* columns solved together; num_probes % it == 0 */
+    int32_t max_iters;       /* cap on Lanczos/CG steps */
+    int32_t fixed_iters;     /* > 0: exactly t steps (Algorithm 1 input t);
+                                0: iterate until rel_tol */
+    int32_t precision;       /* ld_precision */
+    int32_t residual_check;  /* 1: fill ld_result.max_resid (one extra K V pass) */
+    int32_t reserved;
+    uint64_t seed;           /* SplitMix64 seed of the probes when probes_dev is NULL */
+    double rel_tol;          /* stop when max_i ||r_i|| / ||z_i|| < rel_tol (seed system) */
+} ld_options;
+
+typedef struct {
+    double logdet;        /* the estimate: logdet_P + trace_est */
+    double logdet_P;      /* log det P */
+    double trace_est;     /* (1/s) sum_i [b |z_i|^2 + sum_j c_j q_ij] */
+    double std_err;       /* sample std of the per-probe brackets / sqrt(s) */
+    int32_t iters;        /* max CG steps over the probe blocks */
+    int32_t converged;    /* 1 if every column met rel_tol (or fixed_iters ran) */
+    double max_resid[5];  /* residual check: max_i ||z_i - (B + sigma_j) x_ij|| / ||z_i||,
+                             fp64 norms; entries beyond the order are 0 */
+    double final_rel_resid; /* max_i ||r_i|| / ||z_i|| of the seed system at exit */
+} ld_result;
+
+typedef struct ld_precond ld_precond;
+typedef struct ld_surrogate ld_surrogate;
+
+/* ------------------------------------------------------------------- misc */
+const char *ld_status_string(int status);
+/* Reason for the last non-OK status returned on this thread ("" if none). */
+const char *ld_last_error(void);
+int ld_version(void);
+
+/* Partial fractions of r_k (Table 1, derived here from the Eq. 1 closed forms):
+ * r_k(x) = b + sum_{j<k} c[j] / (x + sigma[j]), sigma ascending, c < 0.
+ * b, c, sigma are host pointers (c, sigma of length k). */
+int ld_rk_coeffs(int32_t order, double *b, double *c, double *sigma);
+
+/* ------------------------------------------------------------ kernel product
+ * W = (K(X, X) + noise I) V  -- the matrix-free product Algorithm 1 step 2
+ * spends its O(t n^2) time in (Section 2, complexity paragraph).
+ * X_dev: n-by-d float64.  V_dev, W_dev: n-by-c row-major, float64 for
+ * LD_FP64, float32 otherwise (W_dev must not alias V_dev).  No workspace for
+ * FP64/FP32; TC modes need ld_kz_workspace_size(n, d, c, precision) bytes. */
+size_t ld_kz_workspace_size(int64_t n, int32_t d, int32_t c, int32_t precision);
+int ld_kz(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
+          const void *V_dev, void *W_dev, int32_t c, int32_t precision,
+          void *ws, size_t ws_bytes, void *stream);
+
+/* Same pass computing both W = K V and W_dl = (dK/dl) V (for the gradient,
+ * Section 3's CG-based gradient; derivative forms above).  noise is NOT added
+ * to either.  FP64 and FP32 only. */
+int ld_kz_dl(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
+             const void *V_dev, void *W_dev, void *Wdl_dev, int32_t c,
+             int32_t precision, void *stream);
+
+/* Rademacher block from the SplitMix64 stream (Steele, Lea & Flood 2014):
+ * Z[i, j] (row-major n-by-s int8) uses counter (col0 + j) * n + i and is +1
+ * when bit 63 of the output is 0, else -1 (Algorithm 1 step 1 with D the
+ * Rademacher distribution of Section 3). */
+int ld_rademacher(uint64_t seed, int64_t n, int32_t s, int32_t col0,
+                  int8_t *Z_dev, void *stream);
+
+/* --------------------------------------------------------- preconditioner
+ * P = D + A A^T by randomized truncated SVD (Section 2 "randomized, truncated
+ * SVD" after Halko et al. Alg. 4.1 + 5.3; Section 3: rank, iterations):
+ *   Omega = Rademacher(seed) n-by-rank, Y = M Omega,
+ *   power_iters times: Y = M orth(Y);  Q = orth(Y);  C = Q^T M Q;
+ *   A = Q chol(C);  D = max(diag(M) - rowsumsq(A), max(noise, 1e-12 diag(M))).
+ * The handle stores the split factor L = D^1/2 (I + Q_G (C_P - I) Q_G^T) with
+ * G = D^-1/2 A = Q_G R_G, C_P C_P^T = I + R_G R_G^T, and
+ * log det P = sum log D + 2 sum log diag(C_P).
+ * precision: LD_FP64 keeps factors in float64 (products FP64); any other
+ * value keeps n-by-rank factors in float32, r-by-r factors in float64, and
+ * runs the M products in that precision.
+ * rank = 0 gives P = I (Appendix "Identity"). */
+size_t precond_workspace_size(int64_t n, int32_t d, int32_t rank, int32_t precision);
+int precond_build(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
+                  int32_t rank, int32_t power_iters, uint64_t seed,
+                  int32_t precision, void *ws, size_t ws_bytes, void *stream,
+                  ld_precond **out);
+/* Build the same handle from host A (n-by-rank row-major) and D (n). */
+int precond_import(const double *A_host, const double *D_host, int64_t n,
+                   int32_t rank, int32_t precision, void *stream,
+                   ld_precond **out);
+/* Copy A = D^1/2 Q_G R_G (n-by-rank) and D (n) to host; logdet_P optional. */
+int precond_export(const ld_precond *P, double *A_host, double *D_host,
+                   double *logdet_P, void *stream);
+int precond_info(const ld_precond *P, int64_t *n, int32_t *rank,
+                 int32_t *precision, double *logdet_P);
+/* V_dev (n-by-c) -> W_dev = L^-1 V (transpose = 0) or L^-T V (transpose = 1);
+ * float64 for an LD_FP64 handle, float32 otherwise; W may alias V. */
+int precond_apply(const ld_precond *P, int32_t transpose, const void *V_dev,
+                  void *W_dev, int32_t c, void *stream);
+void precond_free(ld_precond *P);
+
+/* --------------------------------------------------------------- estimator
+ * Algorithm 1 with the shifted solves done by a block multi-shift CG on
+ * B = L^-1 M L^-T (Section 2 multi-shift paragraph, after Jegerlehner): each
+ * probe block runs CG on the seed system B + sigma_min I, the Lanczos
+ * tridiagonal T is rebuilt from the CG coefficients, and
+ * q_ij = |z_i|^2 e_1^T (T_i + (sigma_j - sigma_min) I)^-1 e_1 by a tridiagonal
+ * solve (Algorithm 1 step 3, Thomas), giving
+ *   logdet = log det P + (1/s) sum_i [ b |z_i|^2 + sum_j c_j q_ij ].
+ * P = NULL means P = I.  probes_dev: n-by-num_probes int8 (+-1), or NULL to
+ * draw them with ld_rademacher(opt->seed, ...).  per_probe_host: optional
+ * (num_probes doubles) receives the bracket per probe.
+ * Returns LD_ERR_NOT_CONVERGED (with *out filled) when rel_tol was not met. */
+size_t logdet_workspace_size(int64_t n, int32_t d, const ld_precond *P,
+                             const ld_options *opt);
+int logdet_estimate(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
+                    const ld_precond *P, const ld_options *opt,
+                    const int8_t *probes_dev, double *per_probe_host,
+                    void *ws, size_t ws_bytes, void *stream, ld_result *out);
+
+/* Gradient of the estimator with P and the probes held fixed:
+ *   d/dtheta = (1/s) sum_i sum_j (-c_j) y_ij^T (dM/dtheta) y_ij,
+ *   y_ij = L^-T x_ij,  x_ij = (B + sigma_j I)^-1 z_i,
+ * for theta = (lengthscale, variance, noise) into grad_host[3], plus the
+ * estimate itself in *out.  dM/dl = dK/dl, dM/dv = K/v, dM/dnu = I.
+ * FP64 and FP32 precision only (the derivative pass is SIMT). */
+int logdet_grad(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
+                const ld_precond *P, const ld_options *opt,
+                const int8_t *probes_dev, void *ws, size_t ws_bytes,
+                void *stream, double *grad_host, ld_result *out);
+
+/* --------------------------------------------------------------- surrogate
+ * MLP 4 -> 128 -> 128 -> 128 -> 1 with exact GELU, fp32, trained by Adam on
+ * mean squared error; maps (log l, log v, log nu, log n) to a standardised
+ * log det.  Not part of the paper: an addition for hyperparameter search,
+ * trained on values logdet_estimate produced.  Parameters are one flat
+ * vector: W1 (128x4), b1, W2 (128x128), b2, W3 (128x128), b3, W4 (1x128), b4,
+ * each W row-major (out, in): 33793 floats. */
+int surrogate_create(uint64_t seed, void *stream, ld_surrogate **out);
+int surrogate_set_params(ld_surrogate *S, const float *params_host, void *stream);
+int surrogate_get_params(const ld_surrogate *S, float *params_host, void *stream);
+/* One full-batch gradient: loss and d loss / d params for (theta_dev N-by-4,
+ * y_dev N), written to grad_host (33793) if not NULL. */
+int surrogate_loss_grad(ld_surrogate *S, const float *theta_dev, const float *y_dev,
+                        int32_t N, double *loss_host, float *grad_host, void *stream);
+/* epochs of minibatch Adam (lr, beta1 0.9, beta2 0.999, eps 1e-8) over the
+ * N samples in order (batch rows at a time); final full-batch loss returned. */
+int surrogate_train(ld_surrogate *S, const float *theta_dev, const float *y_dev,
+                    int32_t N, int32_t epochs, int32_t batch, float lr,
+                    void *stream, double *final_loss_host);
+/* out_dev[Q] = f(q), dout_dev[Q*4] = df/dq (may be NULL). */
+int surrogate_infer(const ld_surrogate *S, const float *q_dev, int32_t Q,
+                    float *out_dev, float *dout_dev, void *stream);
+void surrogate_free(ld_surrogate *S);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOGDET_H */

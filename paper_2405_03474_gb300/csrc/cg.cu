@@ -1,0 +1,587 @@
+// The estimator of Algorithm 1 as a block multi-shift conjugate-gradient solve.
+//
+// Section 2 reads steps 2-3 of Algorithm 1 as a multi-shift solver (after
+// Jegerlehner): one Krylov space per probe serves every shifted system
+// (B + sigma_j I) x = z.  Here each block of s probes runs CG on the seed
+// system B + sigma_min I (B = L^-1 M L^-T), all columns at once so the O(n^2)
+// product K V is shared by the block.  CG coefficients (alpha_k, beta_k) give
+// the Lanczos tridiagonal of the seed operator,
+//     T_kk = 1/alpha_k + beta_{k-1}/alpha_{k-1},  T_k,k+1 = sqrt(beta_k)/alpha_k,
+// and the quadratic forms of Algorithm 1 step 3 follow from T alone,
+//     q_ij = |z_i|^2 e_1^T (T_i + (sigma_j - sigma_min) I)^-1 e_1,
+// computed by eliminating the tridiagonal from the bottom (the Thomas
+// algorithm specialised to the first component).  The shifted iterates x_ij
+// are also carried (Jegerlehner's zeta recurrences) for the residual check
+// and the gradient.  All scalar recurrences run in fp64 on the device.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ld {
+
+namespace {
+
+struct ColState {
+    double rho, znorm2, alpha, alpha_prev, beta, beta_prev;
+    double zeta[5], zeta_prev[5], zeta_next[5], alpha_s[5], beta_s[5];
+    int active, upd, t, live[5];
+};
+
+struct Shifts {
+    int m;
+    double delta[5];  // sigma_j - sigma_min
+};
+
+__global__ void cg_init_kernel(ColState *cs, const double *rr, int s, int m) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s) return;
+    ColState st;
+    st.rho = rr[c];
+    st.znorm2 = rr[c];
+    st.alpha = 0.0;
+    st.alpha_prev = 1.0;
+    st.beta = 0.0;
+    st.beta_prev = 0.0;
+    for (int j = 0; j < 5; ++j) {
+        st.zeta[j] = 1.0;
+        st.zeta_prev[j] = 1.0;
+        st.zeta_next[j] = 1.0;
+        st.alpha_s[j] = 0.0;
+        st.beta_s[j] = 0.0;
+        st.live[j] = j < m ? 1 : 0;
+    }
+    st.active = rr[c] > 0.0 ? 1 : 0;
+    st.upd = 0;
+    st.t = 0;
+    cs[c] = st;
+}
+
+// alpha_k = rho_k / p_k^T (B + sigma_min) p_k, and the shifted alpha^sigma_k.
+__global__ void cg_alpha_kernel(ColState *cs, const double *pBp, int s, Shifts sh,
+                                double *hist_a, int max_iters) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s) return;
+    ColState &st = cs[c];
+    st.upd = 0;
+    if (!st.active) {
+        st.alpha = 0.0;
+        for (int j = 0; j < sh.m; ++j) st.alpha_s[j] = 0.0;
+        return;
+    }
+    double a = st.rho / pBp[c];
+    if (!(a > 0.0) || !isfinite(a) || st.t >= max_iters) {  // breakdown: stop this column
+        st.active = 0;
+        st.alpha = 0.0;
+        for (int j = 0; j < sh.m; ++j) st.alpha_s[j] = 0.0;
+        return;
+    }
+    st.alpha = a;
+    st.upd = 1;
+    hist_a[(size_t)st.t * s + c] = a;
+    for (int j = 0; j < sh.m; ++j) {
+        if (!st.live[j]) {
+            st.alpha_s[j] = 0.0;
+            continue;
+        }
+        double den = a * st.beta_prev * (st.zeta_prev[j] - st.zeta[j]) +
+                     st.zeta_prev[j] * st.alpha_prev * (1.0 + sh.delta[j] * a);
+        double zn = st.zeta[j] * st.zeta_prev[j] * st.alpha_prev / den;
+        if (!isfinite(zn) || fabs(zn) < 1e-200) zn = 0.0;
+        st.zeta_next[j] = zn;
+        st.alpha_s[j] = a * zn / st.zeta[j];
+    }
+}
+
+// beta_k = rho_{k+1} / rho_k, shifted beta^sigma_k, convergence test.
+__global__ void cg_beta_kernel(ColState *cs, const double *rr_new, int s, Shifts sh,
+                               double *hist_b, double tol2, int fixed_iters, int *n_active) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < s) {
+        ColState &st = cs[c];
+        if (st.upd) {
+            double rn = rr_new[c];
+            double b = rn / st.rho;
+            if (!isfinite(b)) b = 0.0;
+            st.beta = b;
+            hist_b[(size_t)st.t * s + c] = b;
+            st.t += 1;
+            for (int j = 0; j < sh.m; ++j) {
+                if (!st.live[j]) {
+                    st.beta_s[j] = 0.0;
+                    continue;
+                }
+                double ratio = st.zeta_next[j] / st.zeta[j];
+                st.beta_s[j] = b * ratio * ratio;
+                st.zeta_prev[j] = st.zeta[j];
+                st.zeta[j] = st.zeta_next[j];
+            }
+            st.alpha_prev = st.alpha;
+            st.beta_prev = b;
+            st.rho = rn;
+            if (rn <= 0.0) st.active = 0;
+            if (fixed_iters == 0 && rn < tol2 * st.znorm2) st.active = 0;
+            if (fixed_iters > 0 && st.t >= fixed_iters) st.active = 0;
+        }
+        if (st.active) atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(n_active, cnt);
+}
+
+// r -= alpha Bp;  x_j += alpha^sigma_j p_j   (columns with upd only)
+template <typename T>
+__global__ void cg_update_r_kernel(int64_t n, int s, int m, const ColState *cs, const T *Bp, T *r,
+                                   const T *ps, T *xs) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * s) return;
+    int c = (int)(t % s);
+    const ColState &st = cs[c];
+    if (!st.upd) return;
+    r[t] -= (T)st.alpha * Bp[t];
+    if (xs) {
+        const size_t ns = (size_t)n * s;
+        for (int j = 0; j < m; ++j)
+            if (st.live[j]) xs[j * ns + t] += (T)st.alpha_s[j] * ps[j * ns + t];
+    }
+}
+
+// p = r + beta p;  p_j = zeta_j r + beta^sigma_j p_j
+template <typename T>
+__global__ void cg_update_p_kernel(int64_t n, int s, int m, ColState *cs, const T *r, T *p, T *ps) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * s) return;
+    int c = (int)(t % s);
+    const ColState &st = cs[c];
+    if (!st.upd) return;
+    T rv = r[t];
+    p[t] = rv + (T)st.beta * p[t];
+    if (ps) {
+        const size_t ns = (size_t)n * s;
+        for (int j = 0; j < m; ++j)
+            if (st.live[j]) ps[j * ns + t] = (T)st.zeta[j] * rv + (T)st.beta_s[j] * ps[j * ns + t];
+    }
+}
+
+__global__ void cg_freeze_shifts_kernel(ColState *cs, int s, int m) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s) return;
+    for (int j = 0; j < m; ++j)
+        if (cs[c].live[j] && cs[c].zeta[j] == 0.0) cs[c].live[j] = 0;
+}
+
+// q_cj = |z_c|^2 e_1^T (T_c + delta_j I)^-1 e_1 from the recorded CG coefficients;
+// bracket_c = b |z_c|^2 + sum_j c_j q_cj.
+__global__ void quadrature_kernel(const ColState *cs, const double *hist_a, const double *hist_b,
+                                  int s, RkCoeffs rk, double sigma_min, double *q, double *bracket) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s) return;
+    const ColState &st = cs[c];
+    const int t = st.t;
+    double acc = rk.b * st.znorm2;
+    for (int j = 0; j < rk.m; ++j) {
+        double delta = rk.sigma[j] - sigma_min;
+        double qv = 0.0;
+        if (t > 0) {
+            // bottom-up elimination: d_{t-1} = T_{t-1,t-1} + delta,
+            // d_k = T_kk + delta - T_{k,k+1}^2 / d_{k+1};  e_1^T (T+delta)^-1 e_1 = 1 / d_0
+            int k = t - 1;
+            double ak = hist_a[(size_t)k * s + c];
+            double Tkk = 1.0 / ak + (k > 0 ? hist_b[(size_t)(k - 1) * s + c] / hist_a[(size_t)(k - 1) * s + c] : 0.0);
+            double dd = Tkk + delta;
+            for (k = t - 2; k >= 0; --k) {
+                ak = hist_a[(size_t)k * s + c];
+                double bk = hist_b[(size_t)k * s + c];
+                Tkk = 1.0 / ak + (k > 0 ? hist_b[(size_t)(k - 1) * s + c] / hist_a[(size_t)(k - 1) * s + c] : 0.0);
+                double off2 = bk / (ak * ak);
+                dd = Tkk + delta - off2 / dd;
+            }
+            qv = st.znorm2 / dd;
+        }
+        q[(size_t)c * rk.m + j] = qv;
+        acc += rk.c[j] * qv;
+    }
+    bracket[c] = acc;
+}
+
+// gather probe block columns [col0, col0+s) of an n x S int8 matrix into T
+template <typename T>
+__global__ void gather_probes_kernel(const int8_t *P, int64_t n, int S, int col0, int s, T *Z) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * s) return;
+    int64_t i = t / s;
+    int c = (int)(t % s);
+    Z[t] = (T)P[i * S + col0 + c];
+}
+
+// Xall[i, c*m + j] = x_j[i, c]
+template <typename T>
+__global__ void interleave_kernel(int64_t n, int s, int m, const T *xs, T *Xall) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * s * m) return;
+    int64_t i = t / ((int64_t)s * m);
+    int cj = (int)(t % ((int64_t)s * m));
+    int c = cj / m, j = cj % m;
+    Xall[t] = xs[(size_t)j * n * s + i * s + c];
+}
+
+// R[i, c*m+j] = z[i,c] - BX[i,c*m+j] - sigma_j X[i,c*m+j]
+template <typename T>
+__global__ void residual_kernel(int64_t n, int s, int m, const T *Z, const T *Xall, T *BX,
+                                RkCoeffs rk) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * s * m) return;
+    int64_t i = t / ((int64_t)s * m);
+    int cj = (int)(t % ((int64_t)s * m));
+    int c = cj / m, j = cj % m;
+    BX[t] = Z[i * s + c] - BX[t] - (T)rk.sigma[j] * Xall[t];
+}
+
+inline unsigned nb(int64_t count, int per = 256) { return (unsigned)((count + per - 1) / per); }
+
+template <typename T>
+struct Bufs {
+    T *Xs, *Z, *r, *p, *Bp, *y, *w, *xs, *ps;
+    int8_t *Zi8;
+    double *dots, *part, *hist_a, *hist_b, *q, *bracket;
+    ColState *cs;
+    int *n_active;
+    // precond apply scratch
+    double *Td, *ppart;
+    T *Tt, *Ut;
+    // residual / gradient
+    T *Xall, *Y, *W1, *W2;
+    double *gdots;
+};
+
+// Carve (or measure) the estimator's scratch.
+template <typename T>
+void carve(Arena &a, Bufs<T> &b, int64_t n, int d, const ld_precond *P, int s, int m,
+           int max_iters, int precision, bool vectors, bool extra) {
+    const size_t ns = (size_t)n * s;
+    const int sm = s * m;
+    b.Xs = a.take<T>((size_t)n * d);
+    b.Zi8 = a.take<int8_t>(ns);
+    b.Z = a.take<T>(ns);
+    b.r = a.take<T>(ns);
+    b.p = a.take<T>(ns);
+    b.Bp = a.take<T>(ns);
+    b.y = a.take<T>(ns);
+    b.w = a.take<T>(ns);
+    b.xs = vectors ? a.take<T>(ns * m) : nullptr;
+    b.ps = vectors ? a.take<T>(ns * m) : nullptr;
+    int cw = extra ? std::max(s, sm) : s;
+    b.dots = a.take<double>(4 * (size_t)cw + 64);
+    b.part = a.take<double>(std::max(coldot_partials(n, s), coldot_partials(n, cw)) + 64);
+    b.hist_a = a.take<double>((size_t)max_iters * s + 1);
+    b.hist_b = a.take<double>((size_t)max_iters * s + 1);
+    b.q = a.take<double>((size_t)s * 5);
+    b.bracket = a.take<double>((size_t)s);
+    b.cs = a.take<ColState>((size_t)s);
+    b.n_active = a.take<int>(4);
+    const int r = P ? P->r : 0;
+    b.Td = a.take<double>((size_t)r * cw + 1);
+    // split-K partials are not monotone in the column count: size for each count used
+    size_t pp = gemm_tn_partials(n, r, s);
+    if (extra) pp = std::max(pp, gemm_tn_partials(n, r, sm));
+    b.ppart = a.take<double>(pp + 64);
+    b.Tt = a.take<T>((size_t)r * cw + 1);
+    b.Ut = a.take<T>((size_t)r * cw + 1);
+    if (extra) {
+        b.Xall = a.take<T>(ns * m);
+        b.Y = a.take<T>(ns * m);
+        b.W1 = a.take<T>(ns * m);
+        b.W2 = a.take<T>(ns * m);
+        b.gdots = a.take<double>(8 * (size_t)sm + 64);
+    } else {
+        b.Xall = b.Y = b.W1 = b.W2 = nullptr;
+        b.gdots = nullptr;
+    }
+    a.take<char>(kz_any_workspace<T>(n, d, extra ? std::max(s, sm) : s, precision));
+}
+
+// W = (B + shift) V for a block of c columns.  B = L^-1 (K + noise I) L^-T.
+template <typename T>
+int apply_B(const ld_precond *P, Bufs<T> &b, const T *Xs, int64_t n, int d, const ld_kernel &k,
+            const T *V, T *out, T *tmp1, T *tmp2, int c, double shift, int precision, Arena &a,
+            cudaStream_t st) {
+    if (P) {
+        LD_TRY(precond_apply_impl<T>(P, true, V, tmp1, c, b.Td, b.Tt, b.Ut, b.ppart, st));
+        LD_TRY(kz_any<T>(Xs, n, d, k, tmp1, tmp2, c, precision, a, st));
+        LD_TRY(precond_apply_impl<T>(P, false, tmp2, out, c, b.Td, b.Tt, b.Ut, b.ppart, st));
+    } else {
+        LD_TRY(kz_any<T>(Xs, n, d, k, V, out, c, precision, a, st));
+    }
+    if (shift != 0.0) LD_TRY(axpy<T>((int64_t)n * c, (T)shift, V, out, st));
+    return LD_OK;
+}
+
+struct RunOut {
+    std::vector<double> brackets;
+    int iters = 0;
+    bool converged = true;
+    double final_rel = 0.0;
+    double max_resid[5] = {0, 0, 0, 0, 0};
+    double grad[3] = {0, 0, 0};
+};
+
+template <typename T>
+int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_precond *P,
+             const ld_options &o, const int8_t *probes, void *ws, size_t ws_bytes, cudaStream_t st,
+             bool want_grad, RunOut &out) {
+    RkCoeffs rk;
+    LD_TRY(rk_coeffs(o.order, rk));
+    const int s = o.probes_per_block;
+    const int m = rk.m;
+    const int nblocks = o.num_probes / s;
+    const bool vectors = o.residual_check || want_grad;
+    const int max_iters = o.fixed_iters > 0 ? std::min(o.fixed_iters, o.max_iters) : o.max_iters;
+    Arena meas;
+    meas.measuring = true;
+    Bufs<T> b;
+    carve<T>(meas, b, n, d, P, s, m, max_iters, o.precision, vectors, vectors);
+    Arena a;
+    LD_TRY(arena_open(a, ws, ws_bytes, meas.off));
+    int code = [&]() -> int {
+        carve<T>(a, b, n, d, P, s, m, max_iters, o.precision, vectors, vectors);
+        if (a.overflow) {
+            set_error("internal: estimator workspace overflow");
+            return LD_ERR_WORKSPACE;
+        }
+        LD_TRY(prep_points<T>(X, n, d, point_scale(kern), b.Xs, st));
+        const size_t ns = (size_t)n * s;
+        const double smin = rk.sigma[0];
+        Shifts sh;
+        sh.m = m;
+        for (int j = 0; j < 5; ++j) sh.delta[j] = j < m ? rk.sigma[j] - smin : 0.0;
+        const double tol2 = o.rel_tol * o.rel_tol;
+        out.brackets.assign(o.num_probes, 0.0);
+        for (int blk = 0; blk < nblocks; ++blk) {
+            // probes (Algorithm 1 step 1)
+            if (probes) {
+                gather_probes_kernel<T><<<nb(ns), 256, 0, st>>>(probes, n, o.num_probes, blk * s, s, b.Z);
+                LD_TRY(check_launch("gather_probes"));
+            } else {
+                LD_TRY(rademacher(o.seed, n, s, blk * s, b.Zi8, st));
+                LD_TRY(int8_to<T>(b.Zi8, b.Z, (int64_t)ns, st));
+            }
+            LD_CHECK_CUDA(cudaMemcpyAsync(b.r, b.Z, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            LD_CHECK_CUDA(cudaMemcpyAsync(b.p, b.Z, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            if (vectors) {
+                LD_CHECK_CUDA(cudaMemsetAsync(b.xs, 0, ns * m * sizeof(T), st));
+                for (int j = 0; j < m; ++j)
+                    LD_CHECK_CUDA(cudaMemcpyAsync(b.ps + j * ns, b.Z, ns * sizeof(T),
+                                                  cudaMemcpyDeviceToDevice, st));
+            }
+            LD_TRY(coldot<T>(n, s, b.r, b.r, b.dots, b.part, st));
+            cg_init_kernel<<<nb(s, 128), 128, 0, st>>>(b.cs, b.dots, s, m);
+            LD_TRY(check_launch("cg_init"));
+            int it = 0;
+            for (; it < max_iters; ++it) {
+                // Bp = (B + sigma_min I) p   (the O(n^2) step)
+                LD_TRY(apply_B<T>(P, b, b.Xs, n, d, kern, b.p, b.Bp, b.y, b.w, s, smin, o.precision, a, st));
+                LD_TRY(coldot<T>(n, s, b.p, b.Bp, b.dots, b.part, st));
+                cg_alpha_kernel<<<nb(s, 128), 128, 0, st>>>(b.cs, b.dots, s, sh, b.hist_a, max_iters);
+                cg_update_r_kernel<T><<<nb(ns), 256, 0, st>>>(n, s, m, b.cs, b.Bp, b.r, b.ps, b.xs);
+                LD_TRY(coldot<T>(n, s, b.r, b.r, b.dots + s, b.part, st));
+                LD_CHECK_CUDA(cudaMemsetAsync(b.n_active, 0, sizeof(int), st));
+                cg_beta_kernel<<<nb(s, 128), 128, 0, st>>>(b.cs, b.dots + s, s, sh, b.hist_b, tol2,
+                                                          o.fixed_iters, b.n_active);
+                cg_update_p_kernel<T><<<nb(ns), 256, 0, st>>>(n, s, m, b.cs, b.r, b.p, b.ps);
+                cg_freeze_shifts_kernel<<<nb(s, 128), 128, 0, st>>>(b.cs, s, m);
+                LD_TRY(check_launch("cg iteration"));
+                int n_active = 0;
+                LD_CHECK_CUDA(cudaMemcpyAsync(&n_active, b.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+                LD_CHECK_CUDA(cudaStreamSynchronize(st));
+                if (n_active == 0) {
+                    ++it;
+                    break;
+                }
+            }
+            out.iters = std::max(out.iters, it);
+            quadrature_kernel<<<nb(s, 128), 128, 0, st>>>(b.cs, b.hist_a, b.hist_b, s, rk, smin, b.q,
+                                                         b.bracket);
+            LD_TRY(check_launch("quadrature"));
+            std::vector<ColState> cs(s);
+            LD_CHECK_CUDA(cudaMemcpyAsync(out.brackets.data() + (size_t)blk * s, b.bracket,
+                                          sizeof(double) * s, cudaMemcpyDeviceToHost, st));
+            LD_CHECK_CUDA(cudaMemcpyAsync(cs.data(), b.cs, sizeof(ColState) * s, cudaMemcpyDeviceToHost, st));
+            LD_CHECK_CUDA(cudaStreamSynchronize(st));
+            for (int c = 0; c < s; ++c) {
+                double rel = cs[c].znorm2 > 0 ? sqrt(std::max(cs[c].rho, 0.0) / cs[c].znorm2) : 0.0;
+                out.final_rel = std::max(out.final_rel, rel);
+                if (o.fixed_iters == 0 && !(cs[c].rho < tol2 * cs[c].znorm2) && cs[c].rho > 0)
+                    out.converged = false;
+            }
+            if (!vectors) continue;
+            const int sm = s * m;
+            const size_t nsm = ns * m;
+            interleave_kernel<T><<<nb(nsm), 256, 0, st>>>(n, s, m, b.xs, b.Xall);
+            LD_TRY(check_launch("interleave"));
+            if (o.residual_check) {
+                // ||z - (B + sigma_j) x_j|| / ||z||, one extra pass over all s*m columns
+                LD_TRY(apply_B<T>(P, b, b.Xs, n, d, kern, b.Xall, b.W1, b.Y, b.W2, sm, 0.0, o.precision, a, st));
+                residual_kernel<T><<<nb(nsm), 256, 0, st>>>(n, s, m, b.Z, b.Xall, b.W1, rk);
+                LD_TRY(check_launch("residual"));
+                LD_TRY(coldot<T>(n, sm, b.W1, b.W1, b.gdots, b.part, st));
+                std::vector<double> rn(sm);
+                LD_CHECK_CUDA(cudaMemcpyAsync(rn.data(), b.gdots, sizeof(double) * sm, cudaMemcpyDeviceToHost, st));
+                LD_CHECK_CUDA(cudaStreamSynchronize(st));
+                for (int c = 0; c < s; ++c)
+                    for (int j = 0; j < m; ++j)
+                        out.max_resid[j] = std::max(out.max_resid[j], sqrt(rn[c * m + j] / cs[c].znorm2));
+            }
+            if (want_grad) {
+                // y = L^-T x;  dest/dtheta = (1/s) sum (-c_j) y^T dM y
+                if (P) {
+                    LD_TRY(precond_apply_impl<T>(P, true, b.Xall, b.Y, sm, b.Td, b.Tt, b.Ut, b.ppart, st));
+                } else {
+                    LD_CHECK_CUDA(cudaMemcpyAsync(b.Y, b.Xall, nsm * sizeof(T), cudaMemcpyDeviceToDevice, st));
+                }
+                LD_TRY(kz_dl_simt<T>(b.Xs, n, d, kern.kind, kern.lengthscale, kern.variance, b.Y, b.W1,
+                                     b.W2, sm, st));
+                LD_TRY(coldot<T>(n, sm, b.Y, b.W2, b.gdots, b.part, st));
+                LD_TRY(coldot<T>(n, sm, b.Y, b.W1, b.gdots + sm, b.part, st));
+                LD_TRY(coldot<T>(n, sm, b.Y, b.Y, b.gdots + 2 * sm, b.part, st));
+                std::vector<double> g(3 * sm);
+                LD_CHECK_CUDA(cudaMemcpyAsync(g.data(), b.gdots, sizeof(double) * 3 * sm, cudaMemcpyDeviceToHost, st));
+                LD_CHECK_CUDA(cudaStreamSynchronize(st));
+                for (int c = 0; c < s; ++c)
+                    for (int j = 0; j < m; ++j) {
+                        double w = -rk.c[j] / o.num_probes;
+                        out.grad[0] += w * g[c * m + j];
+                        out.grad[1] += w * g[sm + c * m + j] / kern.variance;
+                        out.grad[2] += w * g[2 * sm + c * m + j];
+                    }
+            }
+        }
+        return LD_OK;
+    }();
+    arena_close(a);
+    return code;
+}
+
+int validate(const double *X, int64_t n, int d, const ld_kernel &k, const ld_precond *P,
+             const ld_options *o, bool grad) {
+    LD_REQUIRE(o != nullptr, "options are NULL");
+    LD_REQUIRE(X != nullptr && n > 0, "need n > 0 points");
+    LD_REQUIRE(d >= 1 && d <= 8, "d must be in [1, 8]");
+    LD_REQUIRE(k.lengthscale > 0 && k.variance > 0 && k.noise >= 0 &&
+                   (k.kind == LD_RBF || k.kind == LD_MATERN52),
+               "bad kernel parameters");
+    LD_REQUIRE(o->order == 1 || o->order == 3 || o->order == 5, "order must be 1, 3 or 5");
+    LD_REQUIRE(o->probes_per_block >= 1 && o->probes_per_block <= 256,
+               "probes_per_block must be in [1, 256]");
+    LD_REQUIRE(o->num_probes >= o->probes_per_block && o->num_probes % o->probes_per_block == 0,
+               "num_probes must be a positive multiple of probes_per_block");
+    LD_REQUIRE(o->max_iters >= 1 && o->max_iters <= 100000, "max_iters must be in [1, 100000]");
+    LD_REQUIRE(o->fixed_iters >= 0, "fixed_iters must be >= 0");
+    LD_REQUIRE(o->fixed_iters > 0 || o->rel_tol > 0, "rel_tol must be > 0 without fixed_iters");
+    LD_REQUIRE(o->precision >= LD_FP64 && o->precision <= LD_F16X3_TC, "bad precision");
+    if (P) {
+        LD_REQUIRE(P->n == n, "preconditioner built for n = %lld, not %lld", (long long)P->n, (long long)n);
+        LD_REQUIRE((P->precision == LD_FP64) == (o->precision == LD_FP64),
+                   "preconditioner and estimate must both be FP64 or both be non-FP64");
+    }
+    if (grad) LD_REQUIRE(o->precision == LD_FP64 || o->precision == LD_FP32,
+                         "logdet_grad supports LD_FP64 and LD_FP32");
+    return LD_OK;
+}
+
+void fill_result(const RunOut &r, const ld_precond *P, const ld_options &o, ld_result *out,
+                 double *per_probe) {
+    double mean = 0.0;
+    for (double v : r.brackets) mean += v;
+    const int S = (int)r.brackets.size();
+    mean /= S;
+    double var = 0.0;
+    for (double v : r.brackets) var += (v - mean) * (v - mean);
+    var = S > 1 ? var / (S - 1) : 0.0;
+    const double ldP = P ? P->logdet_P : 0.0;
+    out->logdet = ldP + mean;
+    out->logdet_P = ldP;
+    out->trace_est = mean;
+    out->std_err = sqrt(var / S);
+    out->iters = r.iters;
+    out->converged = r.converged ? 1 : 0;
+    for (int j = 0; j < 5; ++j) out->max_resid[j] = r.max_resid[j];
+    out->final_rel_resid = r.final_rel;
+    if (per_probe)
+        for (int i = 0; i < S; ++i) per_probe[i] = r.brackets[i];
+    (void)o;
+}
+
+}  // namespace
+
+}  // namespace ld
+
+using namespace ld;
+
+extern "C" {
+
+size_t logdet_workspace_size(int64_t n, int32_t d, const ld_precond *P, const ld_options *opt) {
+    if (!opt) return 0;
+    RkCoeffs rk;
+    if (rk_coeffs(opt->order, rk) != LD_OK) return 0;
+    const int max_iters = opt->fixed_iters > 0 ? std::min(opt->fixed_iters, opt->max_iters) : opt->max_iters;
+    Arena meas;
+    meas.measuring = true;
+    const bool vectors = true;  // enough for residual check and gradient
+    if (opt->precision == LD_FP64) {
+        Bufs<double> b;
+        carve<double>(meas, b, n, d, P, opt->probes_per_block, rk.m, max_iters, opt->precision, vectors, vectors);
+    } else {
+        Bufs<float> b;
+        carve<float>(meas, b, n, d, P, opt->probes_per_block, rk.m, max_iters, opt->precision, vectors, vectors);
+    }
+    return meas.off;
+}
+
+int logdet_estimate(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, const ld_precond *P,
+                    const ld_options *opt, const int8_t *probes_dev, double *per_probe_host,
+                    void *ws, size_t ws_bytes, void *stream, ld_result *out) {
+    clear_error();
+    LD_REQUIRE(out != nullptr, "logdet_estimate: out is NULL");
+    LD_TRY(validate(X_dev, n, d, kern, P, opt, false));
+    RunOut r;
+    cudaStream_t st = (cudaStream_t)stream;
+    int code = opt->precision == LD_FP64
+                   ? run_impl<double>(X_dev, n, d, kern, P, *opt, probes_dev, ws, ws_bytes, st, false, r)
+                   : run_impl<float>(X_dev, n, d, kern, P, *opt, probes_dev, ws, ws_bytes, st, false, r);
+    if (code != LD_OK) return code;
+    fill_result(r, P, *opt, out, per_probe_host);
+    if (!r.converged) {
+        set_error("CG did not reach rel_tol %.3g in %d iterations (final %.3g)", opt->rel_tol,
+                  opt->max_iters, r.final_rel);
+        return LD_ERR_NOT_CONVERGED;
+    }
+    return LD_OK;
+}
+
+int logdet_grad(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, const ld_precond *P,
+                const ld_options *opt, const int8_t *probes_dev, void *ws, size_t ws_bytes,
+                void *stream, double *grad_host, ld_result *out) {
+    clear_error();
+    LD_REQUIRE(out != nullptr && grad_host != nullptr, "logdet_grad: out/grad are NULL");
+    LD_TRY(validate(X_dev, n, d, kern, P, opt, true));
+    RunOut r;
+    cudaStream_t st = (cudaStream_t)stream;
+    int code = opt->precision == LD_FP64
+                   ? run_impl<double>(X_dev, n, d, kern, P, *opt, probes_dev, ws, ws_bytes, st, true, r)
+                   : run_impl<float>(X_dev, n, d, kern, P, *opt, probes_dev, ws, ws_bytes, st, true, r);
+    if (code != LD_OK) return code;
+    fill_result(r, P, *opt, out, nullptr);
+    for (int a = 0; a < 3; ++a) grad_host[a] = r.grad[a];
+    if (!r.converged) {
+        set_error("CG did not reach rel_tol %.3g in %d iterations", opt->rel_tol, opt->max_iters);
+        return LD_ERR_NOT_CONVERGED;
+    }
+    return LD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,191 @@
+// Internal declarations shared by the translation units of liblogdet.so.
+// Public API: include/logdet.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "logdet.h"
+
+namespace ld {
+
+// ------------------------------------------------------------ error state
+void set_error(const char *fmt, ...);
+const char *last_error();
+void clear_error();
+
+#define LD_CHECK_CUDA(...)                                                         \
+    do {                                                                           \
+        cudaError_t e_ = (__VA_ARGS__);                                            \
+        if (e_ != cudaSuccess) {                                                   \
+            ::ld::set_error("%s:%d %s: %s", __FILE__, __LINE__, #__VA_ARGS__,      \
+                            cudaGetErrorString(e_));                               \
+            return LD_ERR_CUDA;                                                    \
+        }                                                                          \
+    } while (0)
+
+#define LD_TRY(...)                                                                \
+    do {                                                                           \
+        int st_ = (__VA_ARGS__);                                                   \
+        if (st_ != LD_OK) return st_;                                              \
+    } while (0)
+
+#define LD_REQUIRE(cond, ...)                                                      \
+    do {                                                                           \
+        if (!(cond)) {                                                             \
+            ::ld::set_error(__VA_ARGS__);                                          \
+            return LD_ERR_INVALID;                                                 \
+        }                                                                          \
+    } while (0)
+
+inline int check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("launch of %s failed: %s", what, cudaGetErrorString(e));
+        return LD_ERR_CUDA;
+    }
+    return LD_OK;
+}
+
+// ------------------------------------------------------------- workspace
+// Bump allocator over caller scratch (or over one cudaMalloc when ws == NULL).
+// Two modes: "measure" (base == nullptr, only counts bytes) and "carve".
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    bool owned = false;
+    bool measuring = false;
+    bool overflow = false;
+
+    template <typename T>
+    T *take(size_t count) {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        size_t at = off;
+        off += bytes;
+        if (measuring) return nullptr;
+        if (off > cap) {
+            overflow = true;
+            return nullptr;
+        }
+        return reinterpret_cast<T *>(base + at);
+    }
+};
+
+// Open an arena over caller scratch, or allocate `need` bytes when ws == NULL.
+int arena_open(Arena &a, void *ws, size_t ws_bytes, size_t need);
+void arena_close(Arena &a);
+
+// ----------------------------------------------------------- coefficients
+struct RkCoeffs {
+    int m = 0;           // number of poles (= order)
+    double b = 0.0;
+    double c[5] = {0};
+    double sigma[5] = {0};  // ascending
+};
+int rk_coeffs(int order, RkCoeffs &out);
+
+// ----------------------------------------------------- kernel evaluation
+// Points are pre-scaled so that the kernel is a function of the squared scaled
+// distance u2 = |xs - ys|^2:
+//   RBF:      xs = x / (l sqrt 2),  k = v exp(-u2)
+//   Matern52: xs = x sqrt(5) / l,   k = v (1 + u + u^2/3) exp(-u), u = sqrt(u2)
+double point_scale(const ld_kernel &k);
+
+template <typename T>
+int prep_points(const double *X, int64_t n, int d, double scale, T *Xs, cudaStream_t st);
+
+// W = (K + noise I) V (SIMT), V, W n-by-c row-major
+template <typename T>
+int kz_simt(const T *Xs, int64_t n, int d, int kind, double variance, double noise,
+            const T *V, T *W, int c, cudaStream_t st);
+// W = K V, Wdl = (dK/dl) V (SIMT, no noise)
+template <typename T>
+int kz_dl_simt(const T *Xs, int64_t n, int d, int kind, double lengthscale, double variance,
+               const T *V, T *W, T *Wdl, int c, cudaStream_t st);
+
+// tensor-core product (float vectors)
+size_t kz_tc_workspace(int64_t n, int d, int c, int precision);
+int kz_tc(const float *Xs, int64_t n, int d, int kind, double variance, double noise,
+          const float *V, float *W, int c, int precision, Arena &ws, cudaStream_t st);
+
+// dispatch on precision: T = double for LD_FP64, float otherwise
+template <typename T>
+int kz_any(const T *Xs, int64_t n, int d, const ld_kernel &k, const T *V, T *W, int c,
+           int precision, Arena &ws, cudaStream_t st);
+template <typename T>
+size_t kz_any_workspace(int64_t n, int d, int c, int precision);
+
+// ------------------------------------------------------------------ BLAS
+// C(m x q) = alpha A(m x k) B(k x q) + beta C, row-major with leading dims.
+template <typename T>
+int gemm_nn(int64_t m, int q, int k, T alpha, const T *A, int64_t lda, const T *B, int64_t ldb,
+            T beta, T *C, int64_t ldc, cudaStream_t st);
+// Cd(p x q) (double) = A(m x p)^T B(m x q), reduction over m split across CTAs
+// with fp64 partials summed in a fixed order.  part: >= splitk_partials(...) doubles.
+size_t gemm_tn_partials(int64_t m, int p, int q);
+template <typename T>
+int gemm_tn(int64_t m, int p, int q, const T *A, int64_t lda, const T *B, int64_t ldb,
+            double *Cd, double *part, cudaStream_t st);
+// out[j] = sum_i A[i*c+j] * B[i*c+j] in fp64, deterministic.
+size_t coldot_partials(int64_t n, int c);
+template <typename T>
+int coldot(int64_t n, int c, const T *A, const T *B, double *out, double *part, cudaStream_t st);
+
+// small helpers
+template <typename Tin, typename Tout>
+int convert(const Tin *in, Tout *out, int64_t count, cudaStream_t st);
+template <typename T>
+int int8_to(const int8_t *in, T *out, int64_t count, cudaStream_t st);
+template <typename T>
+int scale_rows(const T *in, const T *rowscale, T *out, int64_t n, int c, cudaStream_t st);
+template <typename T>
+int axpy(int64_t count, T alpha, const T *x, T *y, cudaStream_t st);  // y += alpha x
+int rademacher(uint64_t seed, int64_t n, int s, int col0, int8_t *Z, cudaStream_t st);
+
+// ------------------------------------------------ small dense (fp64, r x r)
+// In-place lower Cholesky of A (r x r row-major, lower part used) after adding
+// `shift` to the diagonal; *status (device int) = 0 ok, k+1 if pivot k <= 0.
+int dense_chol(double *A, int r, double shift, int *status, cudaStream_t st);
+// Linv = L^-1 for lower-triangular L (r x r), zero above the diagonal.
+int dense_trinv_lower(const double *L, double *Linv, int r, cudaStream_t st);
+// C = alpha op(A) op(B) + beta C for small fp64 matrices (r x r or r x c).
+int dense_gemm(int m, int q, int k, double alpha, const double *A, int lda, bool ta,
+               const double *B, int ldb, bool tb, double beta, double *C, int ldc,
+               cudaStream_t st);
+// out = sum of log(diag(L)) over r entries (device scalar), plus trace helpers.
+int dense_sumlogdiag(const double *L, int r, double *out, cudaStream_t st);
+int dense_trace(const double *A, int r, double *out, cudaStream_t st);
+// A(r x r) <- (A + A^T) / 2
+int dense_symmetrize(double *A, int r, cudaStream_t st);
+// dst (T, r x r) = src (+ add * I), optional transpose
+template <typename T>
+int dense_export(const double *src, T *dst, int r, double add_identity, bool transpose,
+                 cudaStream_t st);
+
+}  // namespace ld
+
+// ---------------------------------------------------- the opaque handles
+struct ld_precond {
+    int64_t n = 0;
+    int r = 0;
+    int precision = LD_FP32;
+    void *Qg = nullptr;       // n x r (T)
+    void *CmI = nullptr;      // r x r (T): C_P^-1 - I
+    void *CmIT = nullptr;     // r x r (T): C_P^-T - I
+    void *dinv_sqrt = nullptr;// n (T)
+    double *D = nullptr;      // n
+    double *RG = nullptr;     // r x r (upper), G = Qg RG
+    double logdet_P = 0.0;
+};
+
+namespace ld {
+// L^-1 / L^-T apply on float or double handles (precond.cu)
+template <typename T>
+int precond_apply_impl(const ld_precond *P, bool transpose, const T *V, T *W, int c, double *Td,
+                       T *Tt, T *Ut, double *part, cudaStream_t st);
+size_t precond_apply_scratch_doubles(const ld_precond *P, int c);
+}  // namespace ld

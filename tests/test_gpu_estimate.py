@@ -1,0 +1,101 @@
+"""Parity of the estimator (Algorithm 1) and its gradient against the oracle,
+on the same probes and the same preconditioner."""
+import numpy as np
+import pytest
+
+from gpu_util import cuda, host, relerr, torch
+from oracle import estimator, gradient, kernels, precond
+from oracle.splitmix import rademacher_block
+from paper_2405_03474_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(n, d, kind, ell, nu, r, seed=0, dist="uniform"):
+    X = inputs.points(n, d, dist, seed=seed)
+    M = kernels.kernel_matrix(X, kind, ell, 1.0, nu)
+    if r > 0:
+        A, D = precond.build(M, rademacher_block(2, n, r), 2, nu)
+    else:
+        A, D = precond.identity(n)
+    F = precond.factors(A, D)
+    B = precond.operator_B(M, F)
+    return X, M, A, D, F, B
+
+
+@pytest.mark.parametrize("order", [1, 3, 5])
+@pytest.mark.parametrize("r", [0, 40])
+def test_converged_fp64_matches_oracle(order, r):
+    n, s = 1100, 8
+    X, M, A, D, F, B = _problem(n, 2, api.MATERN52, 0.2, 1e-2, r)
+    Z = inputs.rademacher(n, s, seed=1)
+    P = api.Precond.import_(A, D, "fp64") if r else None
+    res = api.logdet_estimate(cuda(X), api.Kernel(api.MATERN52, 0.2, 1.0, 1e-2), precond=P,
+                              probes=cuda(Z), order=order, num_probes=s, precision="fp64",
+                              rel_tol=1e-13, max_iters=3000, residual_check=True)
+    est, per_probe, _ = estimator.estimate_converged(B, F["logdet_P"], Z.astype(np.float64), order)
+    assert res["logdet"] == pytest.approx(est, rel=1e-10)
+    np.testing.assert_allclose(res["per_probe"], per_probe, rtol=1e-9)
+    assert max(res["max_resid"][:order]) < 1e-11
+
+
+@pytest.mark.parametrize("order", [1, 3, 5])
+def test_fixed_t_fp64_matches_literal_algorithm1(order):
+    n, s, t = 900, 6, 12
+    X, M, A, D, F, B = _problem(n, 3, api.RBF, 0.5, 1e-2, 24, dist="normal")
+    Z = inputs.rademacher(n, s, seed=2)
+    P = api.Precond.import_(A, D, "fp64")
+    res = api.logdet_estimate(cuda(X), api.Kernel(api.RBF, 0.5, 1.0, 1e-2), precond=P, probes=cuda(Z),
+                              order=order, num_probes=s, precision="fp64", fixed_iters=t, max_iters=t)
+    est, per_probe, _ = estimator.estimate_lanczos(B, F["logdet_P"], Z.astype(np.float64), order, t)
+    assert res["iters"] == t
+    assert res["logdet"] == pytest.approx(est, rel=1e-10)
+
+
+def test_device_probes_match_oracle_splitmix():
+    n, s = 700, 8
+    X, M, A, D, F, B = _problem(n, 2, api.MATERN52, 0.3, 5e-2, 16)
+    P = api.Precond.import_(A, D, "fp64")
+    res = api.logdet_estimate(cuda(X), api.Kernel(api.MATERN52, 0.3, 1.0, 5e-2), precond=P, probes=None,
+                              seed=77, order=3, num_probes=s, probes_per_block=4, precision="fp64",
+                              rel_tol=1e-13, max_iters=2000)
+    Z = rademacher_block(77, n, s)
+    est, _, _ = estimator.estimate_converged(B, F["logdet_P"], Z, 3)
+    assert res["logdet"] == pytest.approx(est, rel=1e-10)
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_converged_fp32_within_1e4(order):
+    n, s = 3000, 16
+    X, M, A, D, F, B = _problem(n, 4, api.MATERN52, 0.25, 1e-2, 64)
+    Z = inputs.rademacher(n, s, seed=3)
+    P = api.Precond.import_(A, D, "fp32")
+    res = api.logdet_estimate(cuda(X), api.Kernel(api.MATERN52, 0.25, 1.0, 1e-2), precond=P,
+                              probes=cuda(Z), order=order, num_probes=s, precision="fp32",
+                              rel_tol=1e-6, max_iters=2000)
+    est, _, _ = estimator.estimate_converged(B, F["logdet_P"], Z.astype(np.float64), order)
+    assert res["logdet"] == pytest.approx(est, rel=1e-4)
+
+
+def test_exact_cases_diagonal_and_M_equal_P():
+    # Huge lengthscale-free check: with P = M the estimate is log det P for every probe.
+    n = 500
+    X, M, A, D, F, B = _problem(n, 2, api.RBF, 0.01, 0.5, 0)  # l tiny: K ~ v I, M ~ (v + nu) I
+    Z = inputs.rademacher(n, 4, seed=4)
+    res = api.logdet_estimate(cuda(X), api.Kernel(api.RBF, 0.01, 1.0, 0.5), probes=cuda(Z), order=3,
+                              num_probes=4, precision="fp64", rel_tol=1e-14, max_iters=500)
+    est, _, _ = estimator.estimate_converged(B, 0.0, Z.astype(np.float64), 3)
+    assert res["logdet"] == pytest.approx(est, rel=1e-12)
+
+
+@pytest.mark.parametrize("kind", [api.RBF, api.MATERN52])
+def test_gradient_fp64_matches_oracle(kind):
+    n, s = 500, 6
+    th = (0.25, 0.9, 2e-2)
+    X, M, A, D, F, B = _problem(n, 2, kind, th[0], th[2], 20)
+    Z = inputs.rademacher(n, s, seed=5)
+    P = api.Precond.import_(A, D, "fp64")
+    res = api.logdet_grad(cuda(X), api.Kernel(kind, *th), precond=P, probes=cuda(Z), order=3,
+                          num_probes=s, precision="fp64", rel_tol=1e-13, max_iters=3000)
+    g = gradient.estimator_grad(X, kind, *th, A, D, Z.astype(np.float64), 3)
+    np.testing.assert_allclose(res["grad"], g, rtol=1e-8)

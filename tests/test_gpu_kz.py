@@ -1,0 +1,70 @@
+"""Parity of the kernel product W = (K + noise I) V against the oracle."""
+import numpy as np
+import pytest
+
+from gpu_util import cuda, host, relerr, torch
+from oracle import kernels, splitmix, coeffs
+from paper_2405_03474_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("kind", [api.RBF, api.MATERN52])
+@pytest.mark.parametrize("n,d,c", [(1000, 2, 16), (333, 3, 5), (777, 4, 33), (64, 1, 1)])
+def test_kz_fp64_matches_dense_oracle(kind, n, d, c):
+    X = inputs.points(n, d, "uniform", seed=3)
+    V = inputs.gaussian(n, c, seed=4)
+    k = api.Kernel(kind, 0.2, 1.3, 1e-2)
+    W = host(api.ld_kz(cuda(X), cuda(V), k, "fp64"))
+    ref = kernels.kernel_matrix(X, kind, 0.2, 1.3, 1e-2) @ V
+    assert relerr(W, ref) < 1e-13
+
+
+@pytest.mark.parametrize("kind", [api.RBF, api.MATERN52])
+def test_kz_fp32_matches_dense_oracle(kind):
+    n, d, c = 1500, 4, 20
+    X = inputs.points(n, d, "uniform", seed=5)
+    V = inputs.gaussian(n, c, seed=6)
+    k = api.Kernel(kind, 0.3, 1.0, 1e-2)
+    W = host(api.ld_kz(cuda(X), cuda(V, torch.float32), k, "fp32"))
+    ref = kernels.kernel_matrix(X, kind, 0.3, 1.0, 1e-2) @ V
+    assert relerr(W, ref) < 2e-6
+
+
+def test_kz_fp32_sampled_rows_at_large_n():
+    n, d, c = 1 << 17, 4, 16
+    X = inputs.points(n, d, "uniform", seed=0)
+    V = inputs.gaussian(n, c, seed=7)
+    k = api.Kernel(api.MATERN52, 0.1, 1.0, 1e-2)
+    W = host(api.ld_kz(cuda(X), cuda(V, torch.float32), k, "fp32"))
+    rows = np.random.default_rng(0).choice(n, 24, replace=False)
+    rows = np.concatenate([rows, [0, n - 1]])
+    ref = kernels.kz_rows(X, V, rows, api.MATERN52, 0.1, 1.0, 1e-2)
+    assert relerr(W[rows], ref) < 5e-6
+
+
+@pytest.mark.parametrize("kind", [api.RBF, api.MATERN52])
+def test_kz_dl_fp64_matches_oracle(kind):
+    n, d, c = 600, 2, 7
+    X = inputs.points(n, d, "uniform", seed=8)
+    V = inputs.gaussian(n, c, seed=9)
+    k = api.Kernel(kind, 0.25, 0.8, 0.0)
+    W, Wdl = api.ld_kz_dl(cuda(X), cuda(V), k, "fp64")
+    assert relerr(host(W), kernels.kernel_matrix(X, kind, 0.25, 0.8, 0.0) @ V) < 1e-13
+    assert relerr(host(Wdl), kernels.dkernel_dl_matrix(X, kind, 0.25, 0.8) @ V) < 1e-13
+
+
+def test_rademacher_bit_exact_with_oracle_splitmix():
+    n, s = 10007, 24
+    Z = host(api.ld_rademacher(12345, n, s, col0=3))
+    ref = splitmix.rademacher_block(12345, n, s, col0=3)
+    np.testing.assert_array_equal(Z.astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("k", [1, 3, 5])
+def test_library_coefficients_match_oracle(k):
+    b, c, s = api.rk_coeffs(k)
+    bo, co, so = coeffs.rk_coeffs(k)
+    assert b == bo
+    np.testing.assert_allclose(s, so, rtol=2e-15)
+    np.testing.assert_allclose(c, co, rtol=2e-14)

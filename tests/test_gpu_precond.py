@@ -1,0 +1,72 @@
+"""Parity of the preconditioner (import, factor, apply, build) against the oracle."""
+import numpy as np
+import pytest
+
+from gpu_util import cuda, host, relerr, torch
+from oracle import kernels, precond
+from oracle.splitmix import rademacher_block
+from paper_2405_03474_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _lowrank(n, r, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, r)) * np.linspace(3.0, 0.2, r)[None, :]
+    D = rng.uniform(0.3, 1.2, n)
+    return A, D
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_import_factor_and_apply(prec, tol):
+    n, r, c = 900, 24, 6
+    A, D = _lowrank(n, r, 0)
+    F = precond.factors(A, D)
+    P = api.Precond.import_(A, D, prec)
+    assert P.logdet_P == pytest.approx(F["logdet_P"], rel=1e-12 if prec == "fp64" else 1e-9)
+    V = inputs.gaussian(n, c, seed=1)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Vt = cuda(V, dt)
+    assert relerr(host(P.apply(Vt, transpose=False)), precond.apply_Linv(F, V)) < tol
+    assert relerr(host(P.apply(Vt, transpose=True)), precond.apply_LinvT(F, V)) < tol
+    A2, D2, ld2 = P.export()
+    np.testing.assert_allclose(D2, D, rtol=1e-15)
+    np.testing.assert_allclose(A2 @ A2.T, A @ A.T, rtol=0, atol=(1e-10 if prec == "fp64" else 1e-4) * np.abs(A @ A.T).max())
+
+
+def test_identity_rank_zero():
+    n = 300
+    P = api.Precond.import_(np.zeros((n, 0)), np.ones(n), "fp64")
+    assert P.logdet_P == 0.0
+    V = cuda(inputs.gaussian(n, 3, seed=2))
+    np.testing.assert_array_equal(host(P.apply(V)), host(V))
+
+
+@pytest.mark.parametrize("kind,dist,ell", [(api.MATERN52, "uniform", 0.2), (api.RBF, "normal", 0.7)])
+def test_build_fp64_matches_oracle_rsvd(kind, dist, ell):
+    # Same Rademacher sketch on both sides (SplitMix64, seed 2): P = D + A A^T agrees.
+    n, d, r, q, nu = 1200, 2, 32, 2, 1e-2
+    X = inputs.points(n, d, dist, seed=0)
+    k = api.Kernel(kind, ell, 1.0, nu)
+    P = api.Precond.build(cuda(X), k, r, power_iters=q, seed=2, precision="fp64")
+    A, D, ldP = P.export()
+    M = kernels.kernel_matrix(X, kind, ell, 1.0, nu)
+    Ao, Do = precond.build(M, rademacher_block(2, n, r), q, nu)
+    np.testing.assert_allclose(D, Do, rtol=1e-9, atol=1e-12)
+    AA, AAo = A @ A.T, Ao @ Ao.T
+    assert np.abs(AA - AAo).max() < 1e-9 * np.abs(AAo).max()
+    assert ldP == pytest.approx(precond.factors(Ao, Do)["logdet_P"], rel=1e-10)
+    # the handle's own factor is consistent with what it exports
+    assert ldP == pytest.approx(precond.factors(A, D)["logdet_P"], rel=1e-12)
+
+
+def test_build_fp32_is_close_to_oracle():
+    n, d, r, q, nu = 2000, 3, 48, 2, 1e-2
+    X = inputs.points(n, d, "uniform", seed=1)
+    k = api.Kernel(api.MATERN52, 0.3, 1.0, nu)
+    P = api.Precond.build(cuda(X), k, r, power_iters=q, seed=2, precision="fp32")
+    A, D, ldP = P.export()
+    M = kernels.kernel_matrix(X, api.MATERN52, 0.3, 1.0, nu)
+    Ao, Do = precond.build(M, rademacher_block(2, n, r), q, nu)
+    assert ldP == pytest.approx(precond.factors(Ao, Do)["logdet_P"], rel=1e-4)
+    assert ldP == pytest.approx(precond.factors(A, D)["logdet_P"], rel=1e-6)
