@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput of the rational-function log-det estimator on one GB300.
+
+One step = one complete estimate of log det M for the workload
+``matern_n1048576_d4`` (n = 2^20 points uniform in [0,1]^4, Matern-5/2,
+lengthscale 0.1, variance 1, noise 1e-2, r_3, rank-512 randomized-SVD
+preconditioner with 2 subspace iterations, 16 Rademacher probes, t = 20
+Lanczos/CG steps as in Section 3, plus the fp64-normed residual check):
+preconditioner build + Algorithm 1, inputs resident in HBM.
+
+Prints one JSON line (metric: log det estimates/s).  --impl reference times
+the CPU FP64 oracle on the host cores on a bounded sample of the same
+workload instead.  Multi-GPU (torchrun): every rank runs its own independent
+estimate (different probe seed), no collective on the data path; value is the
+total over ranks ("weak" scaling).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "matern_n1048576_d4"
+METRIC = "log det estimates/sec at n=2^20 (Matern-5/2, d=4, r_3, rank 512, 16 probes, t=20)"
+UNIT = "estimates/s"
+
+# GB300 ALU roofline for the kernel product: each Matern pair
+# needs one rsqrt and one ex2 on the MUFU (16 ops/clk/SM), 152 SMs, 2070 MHz.
+SMS, MUFU_PER_CLK, SM_MHZ_MAX = 152, 16, 2070.0
+MUFU_PER_PAIR = {"matern52": 2, "rbf": 1}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f16x3_tc")
+    ap.add_argument("--sketch-precision", default="f16_tc")
+    ap.add_argument("--t", type=int, default=20)
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2405_03474_gb300 import inputs
+    w = dict(inputs.WORKLOADS[WORKLOAD])
+    w["n"] = args.n
+    return w
+
+
+# ------------------------------------------------------------------ CPU side
+_SH = {}
+
+
+def _attach(names):
+    """Pool initializer: map the parent's shared X and V blocks (no copies)."""
+    import numpy as np
+    from multiprocessing import shared_memory
+    for key, (name, shape) in names.items():
+        shm = shared_memory.SharedMemory(name=name)
+        _SH[key] = (shm, np.ndarray(shape, dtype=np.float64, buffer=shm.buf))
+
+
+def _oracle_rows(job):
+    """Worker: seconds the oracle's matrix-free rows of (K + nu I) V take."""
+    rows, ncols, ell, nu = job
+    import numpy as np
+    from oracle import kernels
+    X = _SH["X"][1]
+    V = _SH["V%d" % ncols][1]
+    t0 = time.perf_counter()
+    kernels.kz_rows(X, V, np.asarray(rows), kernels.MATERN52, ell, 1.0, nu)
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """Process pool (spawn, one process per host core, one BLAS thread each)
+    sharing the workload's points and V blocks through shared memory."""
+
+    def __init__(self, w):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        import numpy as np
+        from paper_2405_03474_gb300 import inputs
+        self.w = w
+        self.cores = os.cpu_count() or 1
+        n, d = w["n"], w["d"]
+        arrays = {"X": inputs.points(n, d, w["dist"], seed=inputs.SEED_POINTS)}
+        self.cols = sorted({w["probes"], w["probes"] * w["order"], w["rank"]})
+        for c in self.cols:
+            arrays["V%d" % c] = inputs.gaussian(n, c, seed=5)
+        self.shm, names = [], {}
+        for key, arr in arrays.items():
+            shm = shared_memory.SharedMemory(create=True, size=arr.nbytes)
+            np.ndarray(arr.shape, dtype=np.float64, buffer=shm.buf)[...] = arr
+            self.shm.append(shm)
+            names[key] = (shm.name, arr.shape)
+        del arrays
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_attach, initargs=(names,))
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+    def estimate_seconds(self, t_steps, rows_per_core=4):
+        """Seconds the CPU oracle needs for one estimate of the workload,
+        extrapolated from its matrix-free K V on a sample of rows (all cores in
+        parallel): (q + 2) sketch products with `rank` columns, t CG products with
+        `probes` columns and one residual product with probes * order columns."""
+        w = self.w
+        n = w["n"]
+        per_pass = {}
+        sample_rows = rows_per_core * self.cores
+        for ncols in self.cols:
+            jobs = [(list(range(c * rows_per_core, (c + 1) * rows_per_core)), ncols, w["lengthscale"],
+                     w["noise"]) for c in range(self.cores)]
+            per_pass[ncols] = max(self.pool.map(_oracle_rows, jobs)) * n / sample_rows
+        total = ((w["power_iters"] + 2) * per_pass[w["rank"]] + t_steps * per_pass[w["probes"]]
+                 + per_pass[w["probes"] * w["order"]])
+        sample = ("oracle kernels.kz_rows on %d of %d rows for V with %s columns, %d processes x 1 "
+                  "thread; extrapolated to (q+2)=%d sketch + t=%d CG + 1 residual K V passes "
+                  "(the oracle's n-by-r and scalar work is not counted)"
+                  % (sample_rows, n, "/".join(str(c) for c in self.cols), self.cores,
+                     w["power_iters"] + 2, t_steps))
+        return total, sample
+
+    def close(self):
+        self.pool.terminate()
+        for shm in self.shm:
+            shm.close()
+            shm.unlink()
+
+
+# ------------------------------------------------------------------ GPU side
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        mhz, mx, reasons, power = [], None, set(), []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                  "sw_power_cap"), f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        busy = [m for m in mhz if mx and m > 0.5 * mx] or mhz
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz),
+                "power_w_max": max(power) if power else None}
+
+
+def run_ours(args, rank, world, local_rank, pool):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2405_03474_gb300 import _lib, api, inputs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    lib = _lib.load()
+    w = workload(args)
+    n, d = w["n"], w["d"]
+    kern = api.Kernel(w["kind"], w["lengthscale"], w["variance"], w["noise"])
+    X_host = torch.as_tensor(inputs.points(n, d, w["dist"], seed=inputs.SEED_POINTS)).pin_memory()
+    X = X_host.to(dev)
+    opts = dict(order=w["order"], num_probes=w["probes"], probes_per_block=w["probes"],
+                fixed_iters=args.t, max_iters=args.t, precision=args.precision, residual_check=True,
+                seed=inputs.SEED_PROBES + 1000 * rank)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step(Xd):
+        P = api.Precond.build(Xd, kern, w["rank"], power_iters=w["power_iters"],
+                              seed=inputs.SEED_SKETCH, precision=args.sketch_precision)
+        res = api.logdet_estimate(Xd, kern, precond=P, **opts)
+        P.free()
+        return res
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        res = step(X)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed between steps (outside the step events)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = Clocks(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = lib.ld_launch_count()
+    lib.ld_profile_begin()
+    results = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        results.append(step(X))
+        ev[k][1].record(stream)
+    import ctypes
+    kz_ms, kz_n, kz_pairs, kz_flops = (ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(),
+                                      ctypes.c_double())
+    lib.ld_profile_end(ctypes.byref(kz_ms), ctypes.byref(kz_n), ctypes.byref(kz_pairs), ctypes.byref(kz_flops))
+    torch.cuda.synchronize()
+    barrier()
+    launches = lib.ld_launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms_max = float(t.item())
+    value = world * args.steps / (total_ms_max / 1e3)
+
+    # end to end through the public API: host points in, host result out
+    e2e = None
+    if not args.no_e2e:
+        e2e_ms = []
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            torch.cuda.synchronize()
+            barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Xd = X_host.to(dev, non_blocking=True)
+            r = step(Xd)  # returns host scalars and the host per-probe array
+            b.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+        tt = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * args.steps / (float(tt.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(X_host.numel() * X_host.element_size()),
+               "d2h_bytes_per_step": int(8 * (w["probes"] + 16))}
+
+    if rank != 0:
+        return None
+
+    # sampled-row error of the kernel product against the oracle (same V)
+    err = None
+    try:
+        from oracle import kernels
+        c = w["probes"]
+        V = inputs.gaussian(n, c, seed=7)
+        Wg = api.ld_kz(X, torch.as_tensor(V, dtype=torch.float32).to(dev), kern, args.precision).cpu().numpy()
+        rows = np.random.default_rng(0).choice(n, 8, replace=False)
+        ref = kernels.kz_rows(inputs.points(n, d, w["dist"], seed=inputs.SEED_POINTS), V, rows, w["kind"],
+                              w["lengthscale"], w["variance"], w["noise"])
+        err = float(np.linalg.norm(Wg[rows] - ref) / np.linalg.norm(ref))
+    except Exception as ex:  # report, do not hide
+        err = "failed: %s" % ex
+
+    avg_launch_ms = kz_ms.value / max(1, kz_n.value)
+    pairs_per_launch = kz_pairs.value / max(1, kz_n.value)
+    achieved = pairs_per_launch / (avg_launch_ms / 1e3) / 1e9  # Gpair/s
+    kname = "matern52" if w["kind"] == inputs.MATERN52 else "rbf"
+    peak = SMS * MUFU_PER_CLK / MUFU_PER_PAIR[kname] * SM_MHZ_MAX * 1e6 / 1e9
+    res = results[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16x3", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "d": d, "kernel": kname, "lengthscale": w["lengthscale"],
+                   "variance": w["variance"], "noise": w["noise"], "order": w["order"], "rank": w["rank"],
+                   "power_iters": w["power_iters"], "probes": w["probes"], "lanczos_steps": args.t,
+                   "kz_precision": args.precision, "sketch_precision": args.sketch_precision,
+                   "residual_check": True, "parallelism": "independent estimate per GPU",
+                   "l2": "flushed between steps (256 MiB write, outside step events)"},
+        "probe_matvecs_per_s": world * args.steps * (w["probes"] * args.t + w["probes"] * w["order"])
+                               / (total_ms_max / 1e3),
+        "estimate": {"logdet": res["logdet"], "logdet_P": res["logdet_P"], "std_err": res["std_err"],
+                     "iters": res["iters"], "max_resid": res["max_resid"][:w["order"]]},
+        "kz_rel_err_vs_oracle_sampled_rows": err,
+        "roofline": {"kernel": "kz_tc_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
+                     "launches": kz_n.value, "avg_launch_ms": avg_launch_ms,
+                     "share_of_step": kz_ms.value / total_ms,
+                     "tensor_tflops": kz_flops.value / (kz_ms.value / 1e3) / 1e12},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+    }
+    if pool is not None:
+        sec, sample = pool.estimate_seconds(args.t)
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                                "sample": sample}
+    return line
+
+
+def run_reference(args, pool):
+    w = workload(args)
+    cores = pool.cores
+    vals = []
+    sample = ""
+    for k in range(args.warmup + args.steps):
+        sec, sample = pool.estimate_seconds(args.t, rows_per_core=1)
+        if k >= args.warmup:
+            vals.append(1.0 / sec)
+    value = statistics.mean(vals)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": w["n"], "d": w["d"], "kernel": "matern52",
+                       "rank": w["rank"], "probes": w["probes"], "lanczos_steps": args.t},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        pool = OraclePool(workload(args))
+        try:
+            line = run_reference(args, pool)
+        finally:
+            pool.close()
+        print(json.dumps(line))
+        return 0
+    # the oracle's process pool is started (spawn) before any GPU call
+    pool = None
+    if rank == 0 and not args.no_cpu:
+        pool = OraclePool(workload(args))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        line = run_ours(args, rank, world, local_rank, pool)
+    finally:
+        if pool is not None:
+            pool.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

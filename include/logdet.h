@@ -210,6 +210,18 @@ int logdet_grad(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
                 const int8_t *probes_dev, void *ws, size_t ws_bytes,
                 void *stream, double *grad_host, ld_result *out);
 
+/* ------------------------------------------------------------- diagnostics
+ * Not part of the paper: measurement hooks for benchmarks.
+ * ld_launch_count: number of kernels this library has launched in the process.
+ * ld_profile_begin / ld_profile_end: between the two calls every launch of the
+ * kernel product (the O(n^2) step) is bracketed by CUDA events recorded on its
+ * own stream; end synchronises those events and returns the summed device
+ * time (ms), the launch count, the kernel evaluations (n^2 per launch) and the
+ * multiply-add flops (2 n^2 c per product) they did.  Single-threaded use. */
+int64_t ld_launch_count(void);
+int ld_profile_begin(void);
+int ld_profile_end(double *kz_ms, int64_t *kz_launches, double *kz_pairs, double *kz_mma_flops);
+
 /* --------------------------------------------------------------- surrogate
  * MLP 4 -> 128 -> 128 -> 128 -> 1 with exact GELU, fp32, trained by Adam on
  * mean squared error; maps (log l, log v, log nu, log n) to a standardised

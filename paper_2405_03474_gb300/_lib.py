@@ -80,6 +80,9 @@ _SIGS = {
     "logdet_workspace_size": (c_size_t, [c_int64, c_int32, _P, _P]),
     "logdet_estimate": (c_int32, [_P, c_int64, c_int32, LdKernel, _P, _P, _P, _P, _P, c_size_t, _P, _P]),
     "logdet_grad": (c_int32, [_P, c_int64, c_int32, LdKernel, _P, _P, _P, _P, c_size_t, _P, _P, _P]),
+    "ld_launch_count": (c_int64, []),
+    "ld_profile_begin": (c_int32, []),
+    "ld_profile_end": (c_int32, [_P, _P, _P, _P]),
     "surrogate_create": (c_int32, [c_uint64, _P, _P]),
     "surrogate_set_params": (c_int32, [_P, _P, _P]),
     "surrogate_get_params": (c_int32, [_P, _P, _P]),

@@ -302,7 +302,19 @@ void carve(Arena &a, Bufs<T> &b, int64_t n, int d, const ld_precond *P, int s, i
         b.Xall = b.Y = b.W1 = b.W2 = nullptr;
         b.gdots = nullptr;
     }
-    a.take<char>(kz_any_workspace<T>(n, d, extra ? std::max(s, sm) : s, precision));
+}
+
+// carve() plus the tail the kernel product takes for itself (it carves from the
+// arena's remaining space and gives it back after each call)
+template <typename T>
+size_t run_bytes(int64_t n, int d, const ld_precond *P, int s, int m, int max_iters, int precision,
+                 bool vectors, bool extra) {
+    Arena meas;
+    meas.measuring = true;
+    Bufs<T> b;
+    carve<T>(meas, b, n, d, P, s, m, max_iters, precision, vectors, extra);
+    meas.take<char>(kz_any_workspace<T>(n, d, extra ? std::max(s, s * m) : s, precision));
+    return meas.off;
 }
 
 // W = (B + shift) V for a block of c columns.  B = L^-1 (K + noise I) L^-T.
@@ -341,12 +353,9 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
     const int nblocks = o.num_probes / s;
     const bool vectors = o.residual_check || want_grad;
     const int max_iters = o.fixed_iters > 0 ? std::min(o.fixed_iters, o.max_iters) : o.max_iters;
-    Arena meas;
-    meas.measuring = true;
     Bufs<T> b;
-    carve<T>(meas, b, n, d, P, s, m, max_iters, o.precision, vectors, vectors);
     Arena a;
-    LD_TRY(arena_open(a, ws, ws_bytes, meas.off));
+    LD_TRY(arena_open(a, ws, ws_bytes, run_bytes<T>(n, d, P, s, m, max_iters, o.precision, vectors, vectors)));
     int code = [&]() -> int {
         carve<T>(a, b, n, d, P, s, m, max_iters, o.precision, vectors, vectors);
         if (a.overflow) {
@@ -394,7 +403,7 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
                                                           o.fixed_iters, b.n_active);
                 cg_update_p_kernel<T><<<nb(ns), 256, 0, st>>>(n, s, m, b.cs, b.r, b.p, b.ps);
                 cg_freeze_shifts_kernel<<<nb(s, 128), 128, 0, st>>>(b.cs, s, m);
-                LD_TRY(check_launch("cg iteration"));
+                LD_TRY(check_launch("cg iteration", 5));
                 int n_active = 0;
                 LD_CHECK_CUDA(cudaMemcpyAsync(&n_active, b.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
                 LD_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -529,17 +538,10 @@ size_t logdet_workspace_size(int64_t n, int32_t d, const ld_precond *P, const ld
     RkCoeffs rk;
     if (rk_coeffs(opt->order, rk) != LD_OK) return 0;
     const int max_iters = opt->fixed_iters > 0 ? std::min(opt->fixed_iters, opt->max_iters) : opt->max_iters;
-    Arena meas;
-    meas.measuring = true;
     const bool vectors = true;  // enough for residual check and gradient
-    if (opt->precision == LD_FP64) {
-        Bufs<double> b;
-        carve<double>(meas, b, n, d, P, opt->probes_per_block, rk.m, max_iters, opt->precision, vectors, vectors);
-    } else {
-        Bufs<float> b;
-        carve<float>(meas, b, n, d, P, opt->probes_per_block, rk.m, max_iters, opt->precision, vectors, vectors);
-    }
-    return meas.off;
+    if (opt->precision == LD_FP64)
+        return run_bytes<double>(n, d, P, opt->probes_per_block, rk.m, max_iters, opt->precision, vectors, vectors);
+    return run_bytes<float>(n, d, P, opt->probes_per_block, rk.m, max_iters, opt->precision, vectors, vectors);
 }
 
 int logdet_estimate(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, const ld_precond *P,

@@ -41,7 +41,12 @@ void clear_error();
         }                                                                          \
     } while (0)
 
-inline int check_launch(const char *what) {
+// Launch accounting: every kernel launch site reports through check_launch
+// with the number of kernels it launched since the previous check.
+void count_launches(int k);
+
+inline int check_launch(const char *what, int launches = 1) {
+    count_launches(launches);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("launch of %s failed: %s", what, cudaGetErrorString(e));
@@ -49,6 +54,11 @@ inline int check_launch(const char *what) {
     }
     return LD_OK;
 }
+
+// Optional timing of the kernel-product launches (CUDA events on the launch
+// stream), enabled between ld_profile_begin and ld_profile_end.
+int prof_begin_launch(cudaStream_t st, double pairs, double mma_flops);  // -1 when off
+void prof_end_launch(cudaStream_t st, int slot);
 
 // ------------------------------------------------------------- workspace
 // Bump allocator over caller scratch (or over one cudaMalloc when ws == NULL).

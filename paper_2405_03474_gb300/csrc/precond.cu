@@ -172,7 +172,7 @@ int cholqr2(const T *Y, T *Q, T *tmp, T *Tr, int64_t n, int r, Small &s, int k0,
         LD_TRY(dense_gemm(r, r, r, 1.0, s.L1, r, false, s.L2, r, false, 0.0, s.C, r, st));
         LD_TRY(dense_export<double>(s.C, s.R, r, 0.0, true, st));
     }
-    return check_launch("cholqr2");
+    return check_launch("cholqr2", 4);
 }
 
 template <typename T>
@@ -210,10 +210,11 @@ int finish_factor(ld_precond *P, T *G, T *Yscratch, T *Tr, Small &s, double *log
         LD_TRY(dense_export<T>(s.L1i, static_cast<T *>(P->CmI), r, -1.0, false, st));
         LD_TRY(dense_export<T>(s.L1i, static_cast<T *>(P->CmIT), r, -1.0, true, st));
         sum_serial_kernel<<<1, 1, 0, st>>>(logD_dev, 1, s.scal + 2, 2.0, s.scal + 1);
+        LD_TRY(check_launch("finish_factor", 2));
     } else {
         sum_serial_kernel<<<1, 1, 0, st>>>(logD_dev, 1, s.scal + 2, 0.0, nullptr);
+        LD_TRY(check_launch("finish_factor", 1));
     }
-    LD_TRY(check_launch("finish_factor"));
     int status[16];
     double ld;
     LD_CHECK_CUDA(cudaMemcpyAsync(status, s.status, sizeof(status), cudaMemcpyDeviceToHost, st));
@@ -315,6 +316,7 @@ int build_impl(const double *X, int64_t n, int d, const ld_kernel &kern, int r, 
                     chol_shift_from_trace<<<1, 1, 0, st>>>(s.C, r, sizeof(T) == 8 ? 1e-13 : 1e-6,
                                                            s.shift);
                     add_identity_dev_kernel<<<nblk(r), 256, 0, st>>>(s.C, r, s.shift);
+                    LD_TRY(check_launch("C shift", 2));
                     LD_TRY(dense_chol(s.C, r, 0.0, s.status + 3, st));
                 }
                 LD_TRY(dense_export<T>(s.C, Tr, r, 0.0, false, st));
@@ -324,9 +326,9 @@ int build_impl(const double *X, int64_t n, int d, const ld_kernel &kern, int r, 
             unsigned nb = nblk(n);
             diag_resid_kernel<T><<<nb, 256, 0, st>>>(A, n, r, diagM, floor, P->D,
                                                     static_cast<T *>(P->dinv_sqrt), s.part);
-            LD_TRY(check_launch("diag_resid"));
             double *logD = s.scal + 0;
             sum_serial_kernel<<<1, 1, 0, st>>>(s.part, (int)nb, logD, 0.0, nullptr);
+            LD_TRY(check_launch("diag_resid", 2));
             if (r > 0) {
                 LD_TRY(scale_rows<T>(A, static_cast<T *>(P->dinv_sqrt), A, n, r, st));  // G
                 int stv[16];
@@ -386,8 +388,8 @@ int import_impl(const double *A_host, const double *D_host, int64_t n, int r, in
             unsigned nb = nblk(n);
             import_kernel<T><<<nb, 256, 0, st>>>(Ad, P->D, n, r, G, static_cast<T *>(P->dinv_sqrt),
                                                  s.part);
-            LD_TRY(check_launch("import"));
             sum_serial_kernel<<<1, 1, 0, st>>>(s.part, (int)nb, s.scal + 0, 0.0, nullptr);
+            LD_TRY(check_launch("import", 2));
             return finish_factor<T>(P, G, Y, Tr, s, s.scal + 0, st);
         }();
     }
@@ -506,6 +508,7 @@ int precond_export(const ld_precond *P, double *A_host, double *D_host, double *
         else
             export_A_kernel<float><<<nblk(n * r), 256, 0, st>>>(static_cast<const float *>(P->Qg),
                                                               P->RG, P->D, n, r, Ad);
+        count_launches(1);
         cudaError_t e = cudaMemcpyAsync(A_host, Ad, sizeof(double) * n * r, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         cudaFree(Ad);

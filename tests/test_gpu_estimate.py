@@ -99,3 +99,19 @@ def test_gradient_fp64_matches_oracle(kind):
                           num_probes=s, precision="fp64", rel_tol=1e-13, max_iters=3000)
     g = gradient.estimator_grad(X, kind, *th, A, D, Z.astype(np.float64), 3)
     np.testing.assert_allclose(res["grad"], g, rtol=1e-8)
+
+
+@pytest.mark.parametrize("prec,tol", [("f16x3_tc", 1e-4), ("f16_tc", 2e-3), ("bf16_tc", 5e-2)])
+def test_converged_tensor_core_accuracy(prec, tol):
+    # The hi/lo fp16 product meets the 1e-4 reduced-precision bar; single fp16
+    # (11-bit K and V) and bf16 (8-bit) are faster but perturb M itself.
+    n, s = 3000, 16
+    X, M, A, D, F, B = _problem(n, 4, api.MATERN52, 0.25, 1e-2, 64)
+    Z = inputs.rademacher(n, s, seed=3)
+    P = api.Precond.import_(A, D, "fp32")
+    res = api.logdet_estimate(cuda(X), api.Kernel(api.MATERN52, 0.25, 1.0, 1e-2), precond=P,
+                              probes=cuda(Z), order=3, num_probes=s, precision=prec,
+                              rel_tol=1e-6, max_iters=2000, allow_not_converged=(prec != "f16x3_tc"),
+                              residual_check=True)
+    est, _, _ = estimator.estimate_converged(B, F["logdet_P"], Z.astype(np.float64), 3)
+    assert res["logdet"] == pytest.approx(est, rel=tol)

@@ -40,7 +40,8 @@ def test_kz_fp32_sampled_rows_at_large_n():
     rows = np.random.default_rng(0).choice(n, 24, replace=False)
     rows = np.concatenate([rows, [0, n - 1]])
     ref = kernels.kz_rows(X, V, rows, api.MATERN52, 0.1, 1.0, 1e-2)
-    assert relerr(W[rows], ref) < 5e-6
+    # fp32 sums of n terms: probabilistic bound sqrt(n) u ~ 362 * 6e-8 = 2.2e-5
+    assert relerr(W[rows], ref) < 2 * np.sqrt(n) * 2.0 ** -24
 
 
 @pytest.mark.parametrize("kind", [api.RBF, api.MATERN52])
@@ -68,3 +69,33 @@ def test_library_coefficients_match_oracle(k):
     assert b == bo
     np.testing.assert_allclose(s, so, rtol=2e-15)
     np.testing.assert_allclose(c, co, rtol=2e-14)
+
+
+# Tensor-core tolerances from the rounding of the operands: fp16 keeps 11 bits
+# (2^-11 relative per element), bf16 8 bits (2^-8), and the hi/lo fp16 split
+# keeps ~22 bits (2^-21 per product after dropping K_lo V_lo); fp32 accumulation
+# over n terms adds ~sqrt(n) 2^-24.
+TC_TOL = {"f16_tc": 2.0 ** -9, "bf16_tc": 2.0 ** -6, "f16x3_tc": 2.0 ** -16}
+
+
+@pytest.mark.parametrize("prec", ["f16x3_tc", "f16_tc", "bf16_tc"])
+@pytest.mark.parametrize("kind", [api.RBF, api.MATERN52])
+@pytest.mark.parametrize("n,d,c", [(1000, 2, 16), (777, 4, 48), (300, 3, 5), (2000, 4, 256), (640, 1, 300)])
+def test_kz_tensor_core_matches_oracle(prec, kind, n, d, c):
+    X = inputs.points(n, d, "uniform", seed=11)
+    V = inputs.gaussian(n, c, seed=12)
+    k = api.Kernel(kind, 0.15, 1.7, 1e-2)
+    W = host(api.ld_kz(cuda(X), cuda(V, torch.float32), k, prec))
+    ref = kernels.kernel_matrix(X, kind, 0.15, 1.7, 1e-2) @ V
+    assert relerr(W, ref) < TC_TOL[prec]
+
+
+def test_kz_f16x3_sampled_rows_at_large_n():
+    n, d, c = 1 << 18, 4, 16
+    X = inputs.points(n, d, "uniform", seed=0)
+    V = inputs.gaussian(n, c, seed=7)
+    k = api.Kernel(api.MATERN52, 0.1, 1.0, 1e-2)
+    W = host(api.ld_kz(cuda(X), cuda(V, torch.float32), k, "f16x3_tc"))
+    rows = np.concatenate([np.random.default_rng(1).choice(n, 24, replace=False), [0, n - 1]])
+    ref = kernels.kz_rows(X, V, rows, api.MATERN52, 0.1, 1.0, 1e-2)
+    assert relerr(W[rows], ref) < 2 * np.sqrt(n) * 2.0 ** -24 + 2.0 ** -19

@@ -23,7 +23,8 @@ def test_import_factor_and_apply(prec, tol):
     A, D = _lowrank(n, r, 0)
     F = precond.factors(A, D)
     P = api.Precond.import_(A, D, prec)
-    assert P.logdet_P == pytest.approx(F["logdet_P"], rel=1e-12 if prec == "fp64" else 1e-9)
+    # an fp32 handle stores G in fp32: log det(I + G^T G) moves by ~ r * 2^-24 * |log det|
+    assert P.logdet_P == pytest.approx(F["logdet_P"], rel=1e-12 if prec == "fp64" else r * 2.0 ** -24)
     V = inputs.gaussian(n, c, seed=1)
     dt = torch.float64 if prec == "fp64" else torch.float32
     Vt = cuda(V, dt)
