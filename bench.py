@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kz-only", type=int, default=0, metavar="C",
+                    help="profiling aid: run only the kernel product on C columns (2 warm-up + 1 launch)")
     return ap.parse_args()
 
 
@@ -359,8 +361,26 @@ def run_reference(args, pool):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_kz_only(args):
+    """Small case for ncu: the kernel product of the workload on C columns."""
+    import torch
+    from paper_2405_03474_gb300 import api, inputs
+    w = workload(args)
+    X = torch.as_tensor(inputs.points(w["n"], w["d"], w["dist"], seed=inputs.SEED_POINTS)).cuda()
+    V = torch.as_tensor(inputs.gaussian(w["n"], args.kz_only, seed=7), dtype=torch.float32).cuda()
+    kern = api.Kernel(w["kind"], w["lengthscale"], w["variance"], w["noise"])
+    for _ in range(3):
+        W = api.ld_kz(X, V, kern, args.precision)
+    torch.cuda.synchronize()
+    print(json.dumps({"kz_only": True, "n": w["n"], "c": args.kz_only, "precision": args.precision,
+                      "checksum": float(W.double().abs().sum())}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.kz_only:
+        return run_kz_only(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

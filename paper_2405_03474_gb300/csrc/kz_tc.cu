@@ -2,12 +2,15 @@
 //
 // The O(n^2) step of Algorithm 1 (Section 2, complexity paragraph) evaluated
 // matrix-free: each CTA owns 128 rows i and sweeps all points j in tiles of 64.
-//   * 8 "eval" warps compute k(x_i, x_j) on the CUDA cores (fp32 differences,
-//     MUFU rsqrt/ex2), round to fp16 (or bf16), optionally split hi/lo, and
-//     store the 128 x 64 tile into shared memory in the canonical no-swizzle
-//     K-major UMMA layout;
-//   * 1 producer warp streams point tiles X_j and the pre-converted operand
-//     image of V_j into shared memory with cp.async.bulk (mbarrier tx counts);
+//   * 8 "eval" warps compute k(x_i, x_j) on the CUDA cores with packed f32x2
+//     arithmetic on pairs of j (differences, squared distance, polynomial) and
+//     one MUFU rsqrt + ex2 per pair, round to fp16 (or bf16), optionally split
+//     hi/lo, and store the 128 x 64 tile into shared memory in the canonical
+//     no-swizzle K-major UMMA layout (two A buffers);
+//   * 1 producer warp streams point tiles X_j (transposed, padded with far
+//     points whose kernel value is exactly 0) and the pre-converted operand
+//     image of V_j into a deeper ring of shared-memory stages with
+//     cp.async.bulk (mbarrier tx counts);
 //   * 1 MMA warp issues tcgen05.mma (M=128, N=c, K=16) accumulating D = K V in
 //     tensor memory (fp32), and releases each stage with tcgen05.commit;
 //   * at the end the eval warps read D with tcgen05.ld, undo the column
@@ -154,18 +157,69 @@ __device__ __forceinline__ float2 unpack2(uint32_t u) {
     }
 }
 
-// unit-variance kernel value from squared scaled distance
+// ---- packed pair arithmetic (sm_100+ f32x2 FADD/FFMA/FMUL) and raw MUFU ops
+__device__ __forceinline__ uint64_t pk(float2 a) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk(uint64_t r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ float mufu_ex2_neg(float x) {  // 2^-x
+    float r;
+    asm("{\n .reg .f32 t;\n neg.f32 t, %1;\n ex2.approx.ftz.f32 %0, t;\n}" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float mufu_rsqrt(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Unit-variance kernel values of two pairs from their squared scaled distances.
+// The coordinates carry an extra log2(e) factor (Matern) or sqrt(log2 e) (RBF),
+// so the exponential is a bare 2^-x:
+//   Matern: u' = u log2 e,  k = (1 + u' ln2 + u'^2 ln2^2 / 3) 2^-u'
+//   RBF:    u2' = u2 log2 e, k = 2^-u2'
+// u2 starts at 1e-30 so that rsqrt never sees 0.
+constexpr float LN2 = 0.69314718055994531f;
+constexpr float LN2SQ_3 = 0.16015100463940035f;  // (ln 2)^2 / 3
+
 template <int KIND>
-__device__ __forceinline__ float kval_fast(float u2) {
-    if (KIND == LD_RBF) return exp2f(-1.4426950408889634f * u2);
-    float uu = fmaxf(u2, 1e-30f);
-    float u = uu * rsqrtf(uu);
-    float e = exp2f(-1.4426950408889634f * u);
-    return fmaf(fmaf(u, 1.0f / 3.0f, 1.0f), u, 1.0f) * e;
+__device__ __forceinline__ uint64_t kval2(uint64_t u2) {
+    const float2 q = upk(u2);
+    if (KIND == LD_RBF) return pk(make_float2(mufu_ex2_neg(q.x), mufu_ex2_neg(q.y)));
+    const uint64_t rs = pk(make_float2(mufu_rsqrt(q.x), mufu_rsqrt(q.y)));
+    const uint64_t u = mul2(u2, rs);
+    const float2 uf = upk(u);
+    const uint64_t e = pk(make_float2(mufu_ex2_neg(uf.x), mufu_ex2_neg(uf.y)));
+    const uint64_t c2 = pk(make_float2(LN2SQ_3, LN2SQ_3));
+    const uint64_t c1 = pk(make_float2(LN2, LN2));
+    const uint64_t one = pk(make_float2(1.f, 1.f));
+    const uint64_t poly = fma2(fma2(u, c2, c1), u, one);
+    return mul2(poly, e);
 }
 
 struct TcParams {
-    const float *Xp;        // padded points, ntiles*64 x d
+    const float *Xp;        // point tiles: per 64-point tile, d x 64 floats (transposed)
     const uint8_t *img;     // operand image: per tile, nprod x (N x 64) halves
     const float *V;         // original V (n x c, row-major)
     const float *colinv;    // 1 / column scale (N)
@@ -177,54 +231,64 @@ struct TcParams {
     int *err;
 };
 
-// Dynamic shared memory layout (per stage s): A hi/lo | B hi/lo | X tile
+// Dynamic shared memory (from a 1024-aligned base):
+//   [0, 1024)            mbarriers, TMEM address, error word
+//   sa A stages          128 x 64 halves (hi, and lo for hi/lo mode)
+//   sl load stages       V operand image tile + transposed point tile
+//   drained sums         128 x (N + 1) floats (hi/lo mode with N <= 128)
 struct Layout {
-    int stages, nprod_a, nprod_b, a_bytes, b_bytes, x_bytes, stage_bytes, total;
+    int sa, sl, a_bytes, b_bytes, x_bytes, l_bytes, a_off, l_off, acc_off, total;
 };
 
-__host__ __device__ inline Layout make_layout(int N, int d, int nprod, int stages) {
+__host__ __device__ inline Layout make_layout(int N, int d, int nprod, int sl) {
     Layout L;
-    L.stages = stages;
-    L.nprod_a = nprod == 3 ? 2 : 1;
-    L.nprod_b = nprod == 3 ? 2 : 1;
-    L.a_bytes = L.nprod_a * A_BYTES;
-    L.b_bytes = L.nprod_b * N * TJ * 2;
-    L.x_bytes = ((TJ * d * 4 + 127) / 128) * 128;
-    L.stage_bytes = ((L.a_bytes + L.b_bytes + L.x_bytes + 1023) / 1024) * 1024;
-    L.total = 1024 + stages * L.stage_bytes + 1024;  // barriers + alignment slack
-    if (nprod == 3 && N <= DRAIN_MAX_N) L.total += TM * (N + 1) * 4;  // drained partial sums
+    L.sa = 2;
+    L.sl = sl;
+    L.a_bytes = (nprod == 3 ? 2 : 1) * A_BYTES;
+    L.b_bytes = (nprod == 3 ? 2 : 1) * N * TJ * 2;
+    L.x_bytes = TJ * d * 4;
+    L.l_bytes = ((L.b_bytes + L.x_bytes + 1023) / 1024) * 1024;
+    L.a_off = 1024;
+    L.l_off = L.a_off + L.sa * L.a_bytes;
+    L.acc_off = L.l_off + L.sl * L.l_bytes;
+    const int acc = (nprod == 3 && N <= DRAIN_MAX_N) ? TM * (N + 1) * 4 : 0;
+    L.total = L.acc_off + acc + 1024;  // + alignment slack of the dynamic base
     return L;
 }
 
 template <int KIND, int DC, int NPROD, bool BF16, bool DRAIN>
-__global__ void __launch_bounds__(NTHREADS, 1) kz_tc_kernel(TcParams p, Layout L) {
+__global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);          // [stages] loads landed
-    uint64_t *afull = full + 8;                                   // [stages] A tile written
-    uint64_t *empty = afull + 8;                                  // [stages] MMA done with stage
-    uint64_t *done = empty + 8;                                   // final accumulate done
-    uint64_t *cfull = done + 1;                                   // [2] chunk accumulated in TMEM buffer
-    uint64_t *cempty = cfull + 2;                                 // [2] TMEM buffer drained
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);  // [sl] loads landed
+    uint64_t *empty = full + 8;                           // [sl] MMA done with load stage
+    uint64_t *afull = empty + 8;                          // [sa] A tile written
+    uint64_t *aempty = afull + 4;                         // [sa] MMA done with A tile
+    uint64_t *done = aempty + 4;                          // all MMAs done
+    uint64_t *cfull = done + 1;                           // [2] chunk accumulated in TMEM buffer
+    uint64_t *cempty = cfull + 2;                         // [2] TMEM buffer drained
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cempty + 2);
     int *s_err = reinterpret_cast<int *>(tmem_slot + 1);
-    uint8_t *stage0 = smem + 1024;
-    // fp32 partial sums drained from TMEM (DRAIN only): 128 rows x (N + 1)
-    float *sacc = reinterpret_cast<float *>(stage0 + (size_t)L.stages * L.stage_bytes);
+    uint8_t *abase = smem + L.a_off;
+    uint8_t *lbase = smem + L.l_off;
+    float *sacc = reinterpret_cast<float *>(smem + L.acc_off);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int dd = DC > 0 ? DC : p.d;
     const int64_t row0 = (int64_t)blockIdx.x * TM;
-    const int S = L.stages;
+    const int SA = L.sa, SL = L.sl;
     const int T = p.ntiles;
     const int ldacc = p.N + 1;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) {
+        for (int s = 0; s < SL; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&afull[s], NEVAL * 32);
             mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < SA; ++s) {
+            mbar_init(&afull[s], NEVAL * 32);
+            mbar_init(&aempty[s], 1);
         }
         mbar_init(done, 1);
         mbar_init(&cfull[0], 1);
@@ -249,25 +313,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) kz_tc_kernel(TcParams p, Layout L
     const uint32_t tmem = *tmem_slot;
 
     if (warp == NEVAL + 1) {
-        // ---------------- producer: X tile and operand image of V per j-tile
+        // ---------------- producer: point tile and operand image of V per j-tile
         if (lane == 0) {
             const uint32_t xb = (uint32_t)(TJ * dd * 4);
             const uint32_t bb = (uint32_t)L.b_bytes;
             int t = 0;
             for (; t < T; ++t) {
-                const int s = t % S;
-                if (t >= S && !mbar_wait(&empty[s], ((t / S) - 1) & 1)) {
+                const int s = t % SL;
+                if (t >= SL && !mbar_wait(&empty[s], ((t / SL) - 1) & 1)) {
                     atomicOr(s_err, ERR_TIMEOUT);
                     break;
                 }
-                uint8_t *st = stage0 + (size_t)s * L.stage_bytes;
+                uint8_t *st = lbase + (size_t)s * L.l_bytes;
                 mbar_expect_tx(&full[s], xb + bb);
-                bulk_g2s(st + L.a_bytes + L.b_bytes, p.Xp + (size_t)t * TJ * dd, xb, &full[s]);
-                bulk_g2s(st + L.a_bytes, p.img + (size_t)t * bb, bb, &full[s]);
+                bulk_g2s(st, p.img + (size_t)t * bb, bb, &full[s]);
+                bulk_g2s(st + L.b_bytes, p.Xp + (size_t)t * TJ * dd, xb, &full[s]);
             }
-            // drain: every issued copy must land before the CTA may exit
-            for (int u = std::max(0, t - S); u < t; ++u) {
-                if (!mbar_wait(&full[u % S], (u / S) & 1)) atomicOr(s_err, ERR_TIMEOUT);
+            // every issued copy must land before the CTA may exit
+            for (int u = std::max(0, t - SL); u < t; ++u) {
+                if (!mbar_wait(&full[u % SL], (u / SL) & 1)) atomicOr(s_err, ERR_TIMEOUT);
             }
         }
     } else if (warp == NEVAL) {
@@ -277,9 +341,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) kz_tc_kernel(TcParams p, Layout L
             const uint32_t lbo = 128, sbo = 1024;
             const uint32_t bhalf = (uint32_t)(p.N * TJ * 2);
             bool ok = true;
-            int t = 0;
-            for (; t < T && ok; ++t) {
-                const int s = t % S;
+            for (int t = 0; t < T && ok; ++t) {
+                const int sl = t % SL, sa = t % SA;
                 const int k = t / KCH;
                 const bool first = DRAIN ? (t % KCH == 0) : (t == 0);
                 const uint32_t dt = tmem + (DRAIN ? (uint32_t)((k & 1) * p.N) : 0u);
@@ -287,13 +350,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) kz_tc_kernel(TcParams p, Layout L
                     ok = false;
                     break;
                 }
-                if (!mbar_wait(&afull[s], (t / S) & 1)) {
+                if (!mbar_wait(&afull[sa], (t / SA) & 1) || !mbar_wait(&full[sl], (t / SL) & 1)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(stage0 + (size_t)s * L.stage_bytes);
-                const uint32_t b0 = a0 + (uint32_t)L.a_bytes;
+                const uint32_t a0 = smem_u32(abase + (size_t)sa * L.a_bytes);
+                const uint32_t b0 = smem_u32(lbase + (size_t)sl * L.l_bytes);
 #pragma unroll
                 for (int ks = 0; ks < TJ / 16; ++ks) {
                     const uint32_t koff = (uint32_t)ks * 256u;
@@ -307,7 +370,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) kz_tc_kernel(TcParams p, Layout L
                         mma_f16(dt, al, bh, idesc, 1u);
                     }
                 }
-                mma_commit(&empty[s]);
+                mma_commit(&empty[sl]);
+                mma_commit(&aempty[sa]);
                 if (DRAIN && (t % KCH == KCH - 1 || t == T - 1)) mma_commit(&cfull[k & 1]);
             }
             if (!ok) atomicOr(s_err, ERR_TIMEOUT);
@@ -321,11 +385,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) kz_tc_kernel(TcParams p, Layout L
         const int quad = warp & 3;          // TMEM lane quadrant of this warp
         const int halfc = warp >> 2;        // column half handled in drains/epilogue
         const int ncol_half = p.N / 2;
-        float xi0[8], xi1[8];
+        // own coordinates, duplicated into pairs: tiles 2*block and 2*block+1
+        uint64_t xr0[8], xr1[8];
+        {
+            const float *t0 = p.Xp + (size_t)(2 * blockIdx.x) * TJ * dd;
+            const float *t1 = t0 + (size_t)TJ * dd;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            xi0[q] = q < dd ? p.Xp[(row0 + rp) * dd + q] : 0.f;
-            xi1[q] = q < dd ? p.Xp[(row0 + rp + 64) * dd + q] : 0.f;
+            for (int a = 0; a < 8; ++a) {
+                const float v0 = a < dd ? t0[a * TJ + rp] : 0.f;
+                const float v1 = a < dd ? t1[a * TJ + rp] : 0.f;
+                xr0[a] = pk(make_float2(v0, v0));
+                xr1[a] = pk(make_float2(v1, v1));
+            }
         }
         // move chunk k's TMEM buffer into the fp32 partial sums (round to nearest)
         auto drain = [&](int k) -> bool {
@@ -344,9 +415,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) kz_tc_kernel(TcParams p, Layout L
         };
         const int C = (T + KCH - 1) / KCH;  // chunks
         int drained = 0;                     // chunks already drained
+        const uint64_t tiny = pk(make_float2(1e-30f, 1e-30f));
         bool ok = true;
         for (int t = 0; t < T; ++t) {
-            const int s = t % S;
+            const int sl = t % SL, sa = t % SA;
             if (DRAIN && t % KCH == KCH / 2 && t >= KCH + KCH / 2) {
                 // chunk t / KCH - 1 finished half a chunk ago
                 if (!drain(drained)) {
@@ -355,60 +427,57 @@ __global__ void __launch_bounds__(NTHREADS, 1) kz_tc_kernel(TcParams p, Layout L
                 }
                 ++drained;
             }
-            if (!mbar_wait(&full[s], (t / S) & 1)) {
+            if (!mbar_wait(&full[sl], (t / SL) & 1) || (t >= SA && !mbar_wait(&aempty[sa], ((t / SA) - 1) & 1))) {
                 ok = false;
                 break;
             }
-            uint8_t *st = stage0 + (size_t)s * L.stage_bytes;
-            const float *xs = reinterpret_cast<const float *>(st + L.a_bytes + L.b_bytes);
-            const int64_t jbase = (int64_t)t * TJ;
+            uint8_t *ast = abase + (size_t)sa * L.a_bytes;
+            const float *xs = reinterpret_cast<const float *>(lbase + (size_t)sl * L.l_bytes + L.b_bytes);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int kq = jq * 2 + h;  // core-matrix column (8 j values)
-                float k0[8], k1[8];
+                uint32_t w0[4], w1[4];       // 8 halves per row
+                float2 f0[4], f1[4];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int jj = kq * 8 + q;
-                    float u0 = 0.f, u1 = 0.f;
+                for (int q = 0; q < 4; ++q) {
+                    const int jj = kq * 8 + 2 * q;
+                    uint64_t u0 = tiny, u1 = tiny;
 #pragma unroll
                     for (int a = 0; a < 8; ++a) {
                         if (a < dd) {
-                            const float xj = xs[jj * dd + a];
-                            const float d0 = xi0[a] - xj, d1 = xi1[a] - xj;
-                            u0 = fmaf(d0, d0, u0);
-                            u1 = fmaf(d1, d1, u1);
+                            const uint64_t xj = *reinterpret_cast<const uint64_t *>(xs + a * TJ + jj);
+                            const uint64_t d0 = sub2(xr0[a], xj), d1 = sub2(xr1[a], xj);
+                            u0 = fma2(d0, d0, u0);
+                            u1 = fma2(d1, d1, u1);
                         }
                     }
-                    const bool valid = jbase + jj < p.n;
-                    k0[q] = valid ? kval_fast<KIND>(u0) : 0.f;
-                    k1[q] = valid ? kval_fast<KIND>(u1) : 0.f;
+                    f0[q] = upk(kval2<KIND>(u0));
+                    f1[q] = upk(kval2<KIND>(u1));
+                    w0[q] = pack2<BF16>(f0[q].x, f0[q].y);
+                    w1[q] = pack2<BF16>(f1[q].x, f1[q].y);
                 }
-                uint4 h0, h1;
-                h0.x = pack2<BF16>(k0[0], k0[1]); h0.y = pack2<BF16>(k0[2], k0[3]);
-                h0.z = pack2<BF16>(k0[4], k0[5]); h0.w = pack2<BF16>(k0[6], k0[7]);
-                h1.x = pack2<BF16>(k1[0], k1[1]); h1.y = pack2<BF16>(k1[2], k1[3]);
-                h1.z = pack2<BF16>(k1[4], k1[5]); h1.w = pack2<BF16>(k1[6], k1[7]);
                 const int r0i = rp, r1i = rp + 64;
                 const size_t off0 = (size_t)(r0i >> 3) * 1024 + (size_t)kq * 128 + (size_t)(r0i & 7) * 16;
                 const size_t off1 = (size_t)(r1i >> 3) * 1024 + (size_t)kq * 128 + (size_t)(r1i & 7) * 16;
-                *reinterpret_cast<uint4 *>(st + off0) = h0;
-                *reinterpret_cast<uint4 *>(st + off1) = h1;
+                *reinterpret_cast<uint4 *>(ast + off0) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+                *reinterpret_cast<uint4 *>(ast + off1) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
                 if (NPROD == 3) {
-                    uint4 l0, l1;
-                    uint32_t *hp0 = &h0.x, *hp1 = &h1.x, *lp0 = &l0.x, *lp1 = &l1.x;
+                    uint32_t l0[4], l1[4];
 #pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        float2 f0 = unpack2<BF16>(hp0[w]);
-                        float2 f1 = unpack2<BF16>(hp1[w]);
-                        lp0[w] = pack2<BF16>(k0[2 * w] - f0.x, k0[2 * w + 1] - f0.y);
-                        lp1[w] = pack2<BF16>(k1[2 * w] - f1.x, k1[2 * w + 1] - f1.y);
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 b0 = unpack2<BF16>(w0[q]);
+                        const float2 b1 = unpack2<BF16>(w1[q]);
+                        const float2 r0 = upk(sub2(pk(f0[q]), pk(b0)));
+                        const float2 r1 = upk(sub2(pk(f1[q]), pk(b1)));
+                        l0[q] = pack2<BF16>(r0.x, r0.y);
+                        l1[q] = pack2<BF16>(r1.x, r1.y);
                     }
-                    *reinterpret_cast<uint4 *>(st + A_BYTES + off0) = l0;
-                    *reinterpret_cast<uint4 *>(st + A_BYTES + off1) = l1;
+                    *reinterpret_cast<uint4 *>(ast + A_BYTES + off0) = make_uint4(l0[0], l0[1], l0[2], l0[3]);
+                    *reinterpret_cast<uint4 *>(ast + A_BYTES + off1) = make_uint4(l1[0], l1[1], l1[2], l1[3]);
                 }
             }
             fence_async_smem();
-            mbar_arrive(&afull[s]);
+            mbar_arrive(&afull[sa]);
         }
         // ---------------- epilogue
         const bool got = ok && mbar_wait(done, 0);
@@ -453,6 +522,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) kz_tc_kernel(TcParams p, Layout L
                      : "memory");
     }
     if (threadIdx.x == 0 && *s_err) atomicOr(p.err, *s_err);
+}
+
+// Point tiles for the kernel: per 64-point tile, coordinate-major (d x 64) so a
+// pair of neighbouring points is one 8-byte load; coordinates scaled once more
+// by `factor`; points past n are placed at 1e18 so every kernel value with them
+// is exactly 0 (2^-x underflows) and no bounds test is needed.
+__global__ void point_tiles_kernel(const float *Xs, int64_t n, int d, float factor, int64_t ntiles_alloc,
+                                   float *Xp) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)TJ * d;
+    if (idx >= per * ntiles_alloc) return;
+    const int64_t t = idx / per;
+    const int rem = (int)(idx % per);
+    const int a = rem / TJ, jj = rem % TJ;
+    const int64_t i = t * TJ + jj;
+    Xp[idx] = i < n ? Xs[i * d + a] * factor : 1e18f;
 }
 
 // ------------------------------------------------------------ prep kernels
@@ -533,9 +618,13 @@ int chunk_N(int c) {
     return ((N + 15) / 16) * 16;
 }
 
+// Load stages: as many as fit with two CTAs per SM (<= 113 KB each, 16 eval
+// warps per SM); one CTA per SM only if even two stages do not fit.
 int stages_for(int N, int d, int nprod) {
+    for (int s = 6; s >= 2; --s)
+        if (make_layout(N, d, nprod, s).total <= 113 * 1024) return s;
     for (int s = 4; s >= 2; --s)
-        if (make_layout(N, d, nprod, s).total <= 200 * 1024) return s;
+        if (make_layout(N, d, nprod, s).total <= 220 * 1024) return s;
     return 2;
 }
 
@@ -583,7 +672,7 @@ size_t kz_tc_workspace(int64_t n, int d, int c, int precision) {
     const int nprod = nprod_of(precision);
     Arena a;
     a.measuring = true;
-    a.take<float>((size_t)(ntiles * TJ + TM) * d);                  // padded points
+    a.take<float>((size_t)(ntiles + 2) * TJ * d);                    // point tiles
     a.take<uint8_t>((size_t)ntiles * (nprod == 3 ? 2 : 1) * N * TJ * 2);  // operand image
     a.take<float>(MAX_N);                                            // scale
     a.take<float>(MAX_N);                                            // 1/scale
@@ -605,7 +694,7 @@ int kz_tc(const float *Xs, int64_t n, int d, int kind, double variance, double n
     const int Nmax = chunk_N(c);
     // carve from the caller's arena (already sized by kz_any_workspace)
     const size_t mark = ws.off;
-    float *Xp = ws.take<float>((size_t)(ntiles * TJ + TM) * d);
+    float *Xp = ws.take<float>((size_t)(ntiles + 2) * TJ * d);
     uint8_t *img = ws.take<uint8_t>((size_t)ntiles * (nprod == 3 ? 2 : 1) * Nmax * TJ * 2);
     float *scale = ws.take<float>(MAX_N);
     float *colinv = ws.take<float>(MAX_N);
@@ -617,8 +706,14 @@ int kz_tc(const float *Xs, int64_t n, int d, int kind, double variance, double n
         return LD_ERR_WORKSPACE;
     }
     int code = [&]() -> int {
-        LD_CHECK_CUDA(cudaMemsetAsync(Xp, 0, sizeof(float) * (size_t)(ntiles * TJ + TM) * d, st));
-        LD_CHECK_CUDA(cudaMemcpyAsync(Xp, Xs, sizeof(float) * (size_t)n * d, cudaMemcpyDeviceToDevice, st));
+        {
+            // exponentials are evaluated as 2^-x: fold log2(e) into the coordinates
+            const float factor = kind == LD_RBF ? 1.2011224087864498f /* sqrt(log2 e) */
+                                                : 1.4426950408889634f /* log2 e */;
+            const int64_t cnt = (ntiles + 2) * TJ * d;
+            point_tiles_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(Xs, n, d, factor, ntiles + 2, Xp);
+            LD_TRY(check_launch("point_tiles"));
+        }
         LD_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
         for (int c0 = 0; c0 < c; c0 += MAX_N) {
             const int N = chunk_N(std::min(MAX_N, c - c0));
