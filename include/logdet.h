@@ -133,6 +133,22 @@ int ld_kz(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
           const void *V_dev, void *W_dev, int32_t c, int32_t precision,
           void *ws, size_t ws_bytes, void *stream);
 
+/* The same product with no device allocation at all.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc (a plug-in
+ * whose host framework owns all device memory through its own pool, a
+ * latency-critical loop where cudaMalloc/cudaFree would synchronise the device,
+ * a process under a hard device-memory cap).  Scratch comes from one static
+ * __device__ array of ld_kz_static_capacity() bytes (32 MiB) that every GPU
+ * loading the library keeps until process exit; sizes whose scratch
+ * (ld_kz_workspace_size) exceeds it return LD_ERR_WORKSPACE.  The first call on
+ * a device looks up the array's address there (make it before any stream
+ * capture).  All calls share the array: calls that overlap on the GPU race.
+ * Arguments and results are those of ld_kz. */
+size_t ld_kz_static_capacity(void);
+int ld_kz_static(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
+                 const void *V_dev, void *W_dev, int32_t c, int32_t precision,
+                 void *stream);
+
 /* Same pass computing both W = K V and W_dl = (dK/dl) V (for the gradient,
  * Section 3's CG-based gradient; derivative forms above).  noise is NOT added
  * to either.  FP64 and FP32 only. */

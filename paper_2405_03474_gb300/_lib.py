@@ -67,6 +67,8 @@ _SIGS = {
     "ld_rk_coeffs": (c_int32, [c_int32, _P, _P, _P]),
     "ld_kz_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int32]),
     "ld_kz": (c_int32, [_P, c_int64, c_int32, LdKernel, _P, _P, c_int32, c_int32, _P, c_size_t, _P]),
+    "ld_kz_static_capacity": (c_size_t, []),
+    "ld_kz_static": (c_int32, [_P, c_int64, c_int32, LdKernel, _P, _P, c_int32, c_int32, _P]),
     "ld_kz_dl": (c_int32, [_P, c_int64, c_int32, LdKernel, _P, _P, _P, c_int32, c_int32, _P]),
     "ld_rademacher": (c_int32, [c_uint64, c_int64, c_int32, c_int32, _P, _P]),
     "precond_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int32]),
