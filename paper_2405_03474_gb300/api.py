@@ -249,3 +249,76 @@ def logdet_grad(X, kernel, precond=None, probes=None, stream=None, allow_not_con
     out = _result_dict(res, st)
     out["grad"] = np.array(g[:])
     return out
+
+
+N_SURROGATE_PARAMS = 33793
+
+
+class Surrogate:
+    """Owner of an ld_surrogate handle: the 4-128-128-128-1 GELU MLP that maps
+    (log lengthscale, log variance, log noise, log n) to log det / n."""
+
+    def __init__(self, seed=0, stream=None):
+        lib = _lib.load()
+        h = ctypes.c_void_p()
+        check(lib.surrogate_create(seed, _stream(stream), ctypes.byref(h)), "surrogate_create")
+        self._h = h
+
+    def set_params(self, flat, stream=None):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == N_SURROGATE_PARAMS
+        check(_lib.load().surrogate_set_params(self._h, flat.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+              "surrogate_set_params")
+
+    def get_params(self, stream=None):
+        flat = np.zeros(N_SURROGATE_PARAMS, dtype=np.float32)
+        check(_lib.load().surrogate_get_params(self._h, flat.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+              "surrogate_get_params")
+        return flat
+
+    @staticmethod
+    def _f32(t, cols):
+        _need_cuda(t)
+        if t.dtype != torch.float32:
+            raise ValueError("surrogate tensors are float32")
+        if cols and (t.dim() != 2 or t.shape[1] != cols):
+            raise ValueError("expected N-by-%d" % cols)
+        return t
+
+    def loss_grad(self, theta, y, stream=None):
+        self._f32(theta, 4)
+        self._f32(y, 0)
+        loss = ctypes.c_double()
+        g = np.zeros(N_SURROGATE_PARAMS, dtype=np.float32)
+        check(_lib.load().surrogate_loss_grad(self._h, _ptr(theta), _ptr(y), theta.shape[0], ctypes.byref(loss),
+                                              g.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+              "surrogate_loss_grad")
+        return loss.value, g
+
+    def train(self, theta, y, epochs, batch, lr=1e-3, stream=None):
+        self._f32(theta, 4)
+        self._f32(y, 0)
+        loss = ctypes.c_double()
+        check(_lib.load().surrogate_train(self._h, _ptr(theta), _ptr(y), theta.shape[0], epochs, batch,
+                                          ctypes.c_float(lr), _stream(stream), ctypes.byref(loss)),
+              "surrogate_train")
+        return loss.value
+
+    def infer(self, q, want_grad=False, stream=None):
+        self._f32(q, 4)
+        out = torch.empty(q.shape[0], dtype=torch.float32, device=q.device)
+        dout = torch.empty_like(q) if want_grad else None
+        check(_lib.load().surrogate_infer(self._h, _ptr(q), q.shape[0], _ptr(out), _ptr(dout), _stream(stream)),
+              "surrogate_infer")
+        return (out, dout) if want_grad else out
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            _lib.load().surrogate_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -157,32 +157,8 @@ __device__ __forceinline__ float2 unpack2(uint32_t u) {
     }
 }
 
-// ---- packed pair arithmetic (sm_100+ f32x2 FADD/FFMA/FMUL) and raw MUFU ops
-__device__ __forceinline__ uint64_t pk(float2 a) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
-    return r;
-}
-__device__ __forceinline__ float2 upk(uint64_t r) {
-    float2 a;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
-    return a;
-}
-__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
-    uint64_t r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-    uint64_t r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
+// ---- raw MUFU ops (one instruction each; packed f32x2 arithmetic uses the
+// sm_100 float2 builtins __fadd2_rn / __ffma2_rn / __fmul2_rn)
 __device__ __forceinline__ float mufu_ex2_neg(float x) {  // 2^-x
     float r;
     asm("{\n .reg .f32 t;\n neg.f32 t, %1;\n ex2.approx.ftz.f32 %0, t;\n}" : "=f"(r) : "f"(x));
@@ -204,18 +180,14 @@ constexpr float LN2 = 0.69314718055994531f;
 constexpr float LN2SQ_3 = 0.16015100463940035f;  // (ln 2)^2 / 3
 
 template <int KIND>
-__device__ __forceinline__ uint64_t kval2(uint64_t u2) {
-    const float2 q = upk(u2);
-    if (KIND == LD_RBF) return pk(make_float2(mufu_ex2_neg(q.x), mufu_ex2_neg(q.y)));
-    const uint64_t rs = pk(make_float2(mufu_rsqrt(q.x), mufu_rsqrt(q.y)));
-    const uint64_t u = mul2(u2, rs);
-    const float2 uf = upk(u);
-    const uint64_t e = pk(make_float2(mufu_ex2_neg(uf.x), mufu_ex2_neg(uf.y)));
-    const uint64_t c2 = pk(make_float2(LN2SQ_3, LN2SQ_3));
-    const uint64_t c1 = pk(make_float2(LN2, LN2));
-    const uint64_t one = pk(make_float2(1.f, 1.f));
-    const uint64_t poly = fma2(fma2(u, c2, c1), u, one);
-    return mul2(poly, e);
+__device__ __forceinline__ float2 kval2(float2 u2) {
+    if (KIND == LD_RBF) return make_float2(mufu_ex2_neg(u2.x), mufu_ex2_neg(u2.y));
+    const float2 rs = make_float2(mufu_rsqrt(u2.x), mufu_rsqrt(u2.y));
+    const float2 u = __fmul2_rn(u2, rs);
+    const float2 e = make_float2(mufu_ex2_neg(u.x), mufu_ex2_neg(u.y));
+    const float2 poly = __ffma2_rn(__ffma2_rn(u, make_float2(LN2SQ_3, LN2SQ_3), make_float2(LN2, LN2)), u,
+                                   make_float2(1.f, 1.f));
+    return __fmul2_rn(poly, e);
 }
 
 struct TcParams {
@@ -385,17 +357,17 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
         const int quad = warp & 3;          // TMEM lane quadrant of this warp
         const int halfc = warp >> 2;        // column half handled in drains/epilogue
         const int ncol_half = p.N / 2;
-        // own coordinates, duplicated into pairs: tiles 2*block and 2*block+1
-        uint64_t xr0[8], xr1[8];
+        // own coordinates, negated and duplicated into pairs: tiles 2*block and 2*block+1
+        float2 xr0[8], xr1[8];
         {
             const float *t0 = p.Xp + (size_t)(2 * blockIdx.x) * TJ * dd;
             const float *t1 = t0 + (size_t)TJ * dd;
 #pragma unroll
             for (int a = 0; a < 8; ++a) {
-                const float v0 = a < dd ? t0[a * TJ + rp] : 0.f;
-                const float v1 = a < dd ? t1[a * TJ + rp] : 0.f;
-                xr0[a] = pk(make_float2(v0, v0));
-                xr1[a] = pk(make_float2(v1, v1));
+                const float v0 = a < dd ? -t0[a * TJ + rp] : 0.f;
+                const float v1 = a < dd ? -t1[a * TJ + rp] : 0.f;
+                xr0[a] = make_float2(v0, v0);
+                xr1[a] = make_float2(v1, v1);
             }
         }
         // move chunk k's TMEM buffer into the fp32 partial sums (round to nearest)
@@ -415,7 +387,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
         };
         const int C = (T + KCH - 1) / KCH;  // chunks
         int drained = 0;                     // chunks already drained
-        const uint64_t tiny = pk(make_float2(1e-30f, 1e-30f));
+        const float2 tiny = make_float2(1e-30f, 1e-30f);
         bool ok = true;
         for (int t = 0; t < T; ++t) {
             const int sl = t % SL, sa = t % SA;
@@ -441,18 +413,18 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int jj = kq * 8 + 2 * q;
-                    uint64_t u0 = tiny, u1 = tiny;
+                    float2 u0 = tiny, u1 = tiny;
 #pragma unroll
                     for (int a = 0; a < 8; ++a) {
                         if (a < dd) {
-                            const uint64_t xj = *reinterpret_cast<const uint64_t *>(xs + a * TJ + jj);
-                            const uint64_t d0 = sub2(xr0[a], xj), d1 = sub2(xr1[a], xj);
-                            u0 = fma2(d0, d0, u0);
-                            u1 = fma2(d1, d1, u1);
+                            const float2 xj = *reinterpret_cast<const float2 *>(xs + a * TJ + jj);
+                            const float2 d0 = __fadd2_rn(xj, xr0[a]), d1 = __fadd2_rn(xj, xr1[a]);
+                            u0 = __ffma2_rn(d0, d0, u0);
+                            u1 = __ffma2_rn(d1, d1, u1);
                         }
                     }
-                    f0[q] = upk(kval2<KIND>(u0));
-                    f1[q] = upk(kval2<KIND>(u1));
+                    f0[q] = kval2<KIND>(u0);
+                    f1[q] = kval2<KIND>(u1);
                     w0[q] = pack2<BF16>(f0[q].x, f0[q].y);
                     w1[q] = pack2<BF16>(f1[q].x, f1[q].y);
                 }
@@ -463,12 +435,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
                 *reinterpret_cast<uint4 *>(ast + off1) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
                 if (NPROD == 3) {
                     uint32_t l0[4], l1[4];
+                    const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float2 b0 = unpack2<BF16>(w0[q]);
-                        const float2 b1 = unpack2<BF16>(w1[q]);
-                        const float2 r0 = upk(sub2(pk(f0[q]), pk(b0)));
-                        const float2 r1 = upk(sub2(pk(f1[q]), pk(b1)));
+                        const float2 r0 = __ffma2_rn(unpack2<BF16>(w0[q]), m1, f0[q]);  // k - hi
+                        const float2 r1 = __ffma2_rn(unpack2<BF16>(w1[q]), m1, f1[q]);
                         l0[q] = pack2<BF16>(r0.x, r0.y);
                         l1[q] = pack2<BF16>(r1.x, r1.y);
                     }

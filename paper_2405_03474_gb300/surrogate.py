@@ -1,0 +1,140 @@
+"""Surrogate of log det over GP hyperparameters, trained on the estimator's own values.
+
+An addition to the paper's method for hyperparameter search: the MLP of
+``csrc/mlp.cu`` maps (log lengthscale, log variance, log noise, log n) to
+log det M / n.  Labels come from ``logdet_estimate`` (r_3, randomized-SVD
+preconditioner) on the GPU; the estimator stays the fallback (queries outside
+the training box) and the judge (audits on random queries).
+
+Run ``python -m paper_2405_03474_gb300.surrogate --help`` for the label job of the
+``surrogate_matern_n262144_d3`` workload (checkpointed to an .npz, resumable).
+"""
+import argparse
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import api, inputs
+
+
+def features(theta, n):
+    """(K x 3) hyperparameters (l, v, nu) -> (K x 4) float32 network inputs."""
+    theta = np.asarray(theta, dtype=np.float64)
+    logn = np.full((theta.shape[0], 1), np.log(float(n)))
+    return np.hstack([np.log(theta), logn]).astype(np.float32)
+
+
+def in_box(theta, box=inputs.THETA_BOX, slack=1e-9):
+    """Mask of hyperparameters inside the training box."""
+    theta = np.asarray(theta, dtype=np.float64)
+    lo = np.array([box["lengthscale"][0], box["variance"][0], box["noise"][0]]) * (1 - slack)
+    hi = np.array([box["lengthscale"][1], box["variance"][1], box["noise"][1]]) * (1 + slack)
+    return np.all((theta >= lo) & (theta <= hi), axis=1)
+
+
+class Estimator:
+    """The plain estimator at one point cloud: log det M(theta) / n on the GPU."""
+
+    def __init__(self, X, kind, rank=64, power_iters=1, probes=16, t=20, order=3, precision="f16x3_tc",
+                 sketch_precision="f16_tc", seed=1):
+        self.X = X
+        self.n = X.shape[0]
+        self.kind, self.rank, self.power_iters = kind, rank, power_iters
+        self.opts = dict(order=order, num_probes=probes, probes_per_block=probes, fixed_iters=t, max_iters=t,
+                         precision=precision, seed=seed)
+        self.sketch_precision = sketch_precision
+
+    def __call__(self, theta):
+        l, v, nu = (float(x) for x in theta)
+        kern = api.Kernel(self.kind, l, v, nu)
+        P = api.Precond.build(self.X, kern, self.rank, power_iters=self.power_iters, seed=inputs.SEED_SKETCH,
+                              precision=self.sketch_precision)
+        try:
+            res = api.logdet_estimate(self.X, kern, precond=P, **self.opts)
+        finally:
+            P.free()
+        return res["logdet"] / self.n
+
+
+def generate_labels(est, thetas, checkpoint=None, every=32, log=None):
+    """Labels est(theta) for each row of thetas, saved every `every` labels to
+    `checkpoint` (.npz with thetas, labels, done) and resumed from it."""
+    thetas = np.asarray(thetas, dtype=np.float64)
+    labels = np.full(len(thetas), np.nan)
+    done = 0
+    if checkpoint and os.path.exists(checkpoint):
+        z = np.load(checkpoint)
+        if z["thetas"].shape == thetas.shape and np.array_equal(z["thetas"], thetas):
+            labels[:] = z["labels"]
+            done = int(z["done"])
+    t0 = time.perf_counter()
+    for i in range(done, len(thetas)):
+        labels[i] = est(thetas[i])
+        if checkpoint and ((i + 1) % every == 0 or i + 1 == len(thetas)):
+            np.savez(checkpoint + ".tmp.npz", thetas=thetas, labels=labels, done=i + 1)
+            os.replace(checkpoint + ".tmp.npz", checkpoint)
+            if log:
+                log("labels %d/%d (%.1f s)" % (i + 1, len(thetas), time.perf_counter() - t0))
+    return labels
+
+
+class HyperSurrogate:
+    """Trained network plus the estimator as fallback and judge."""
+
+    def __init__(self, est, box=inputs.THETA_BOX, seed=0):
+        self.est = est
+        self.box = box
+        self.net = api.Surrogate(seed=seed)
+        self.device = est.X.device
+
+    def fit(self, thetas, labels, epochs=400, batch=256, lr=2e-3):
+        f = torch.as_tensor(features(thetas, self.est.n)).to(self.device)
+        y = torch.as_tensor(np.asarray(labels, dtype=np.float32)).to(self.device)
+        return self.net.train(f, y, epochs=epochs, batch=batch, lr=lr)
+
+    def predict(self, thetas, want_grad=False):
+        """log det / n for each theta; the estimator answers queries outside the box.
+        With want_grad, also d(log det / n)/d(log l, log v, log nu)."""
+        thetas = np.asarray(thetas, dtype=np.float64)
+        f = torch.as_tensor(features(thetas, self.est.n)).to(self.device)
+        if want_grad:
+            out, dout = self.net.infer(f, want_grad=True)
+            g = dout.cpu().numpy()[:, :3].astype(np.float64)
+        else:
+            out = self.net.infer(f)
+            g = None
+        pred = out.cpu().numpy().astype(np.float64)
+        outside = ~in_box(thetas, self.box)
+        for i in np.nonzero(outside)[0]:
+            pred[i] = self.est(thetas[i])
+        return (pred, g, outside) if want_grad else (pred, outside)
+
+    def audit(self, thetas, tol):
+        """Compare against the estimator on `thetas`; returns (max abs error, passed)."""
+        pred, _ = self.predict(thetas)
+        ref = np.array([self.est(t) for t in thetas])
+        err = float(np.max(np.abs(pred - ref)))
+        return err, err <= tol
+
+
+def main():
+    ap = argparse.ArgumentParser(description="label job of the surrogate workload (checkpointed)")
+    ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--checkpoint", default="surrogate_labels.npz")
+    ap.add_argument("--rank", type=int, default=None)
+    ap.add_argument("--t", type=int, default=20)
+    args = ap.parse_args()
+    w = inputs.WORKLOADS["surrogate_matern_n262144_d3"]
+    n = args.n or w["n"]
+    X = torch.as_tensor(inputs.points(n, w["d"], "uniform", seed=inputs.SEED_POINTS)).cuda()
+    est = Estimator(X, w["kind"], rank=args.rank or w["rank"], power_iters=w["power_iters"], probes=w["probes"],
+                    t=args.t)
+    thetas = inputs.sobol_theta(args.count, seed=0)
+    generate_labels(est, thetas, checkpoint=args.checkpoint, log=print)
+
+
+if __name__ == "__main__":
+    main()
