@@ -30,10 +30,22 @@ WORKLOAD = "matern_n1048576_d4"
 METRIC = "log det estimates/sec at n=2^20 (Matern-5/2, d=4, r_3, rank 512, 16 probes, t=20)"
 UNIT = "estimates/s"
 
-# GB300 ALU roofline for the kernel product: each Matern pair
-# needs one rsqrt and one ex2 on the MUFU (16 ops/clk/SM), 152 SMs, 2070 MHz.
-SMS, MUFU_PER_CLK, SM_MHZ_MAX = 152, 16, 2070.0
-MUFU_PER_PAIR = {"matern52": 2, "rbf": 1}
+# GB300 ALU roofline for the kernel product (derivation in the design doc): per SM and
+# clock, 128 fp32 lane-ops, 32 MUFU ex2 and 16 MUFU sqrt; 152 SMs at 2070 MHz.
+# Algorithmic work per pair (i, j): Matern-5/2 d coordinate differences and
+# squares, two FMAs of the polynomial and one product (2d + 3 fp32 ops), one
+# sqrt and one ex2; RBF 2d fp32 ops and one ex2.
+SMS, SM_MHZ_MAX, FP32_PER_CLK, EX2_PER_CLK, SQRT_PER_CLK = 152, 2070.0, 128, 32, 16
+
+
+def pair_peak_gps(kind, d):
+    """Peak kernel-pair evaluations per second (Gpair/s) of the ALU roofline."""
+    if kind == "matern52":
+        fp32, mufu_clk = 2 * d + 3, 1.0 / SQRT_PER_CLK + 1.0 / EX2_PER_CLK
+    else:
+        fp32, mufu_clk = 2 * d, 1.0 / EX2_PER_CLK
+    per_clk = min(FP32_PER_CLK / fp32, 1.0 / mufu_clk)
+    return SMS * per_clk * SM_MHZ_MAX * 1e6 / 1e9
 
 
 def parse():
@@ -309,7 +321,7 @@ def run_ours(args, rank, world, local_rank, pool):
     pairs_per_launch = kz_pairs.value / max(1, kz_n.value)
     achieved = pairs_per_launch / (avg_launch_ms / 1e3) / 1e9  # Gpair/s
     kname = "matern52" if w["kind"] == inputs.MATERN52 else "rbf"
-    peak = SMS * MUFU_PER_CLK / MUFU_PER_PAIR[kname] * SM_MHZ_MAX * 1e6 / 1e9
+    peak = pair_peak_gps(kname, d)
     res = results[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -4,7 +4,7 @@
 // matrix-free: each CTA owns 128 rows i and sweeps all points j in tiles of 64.
 //   * 8 "eval" warps compute k(x_i, x_j) on the CUDA cores with packed f32x2
 //     arithmetic on pairs of j (differences, squared distance, polynomial) and
-//     one MUFU rsqrt + ex2 per pair, round to fp16 (or bf16), optionally split
+//     one MUFU sqrt + ex2 per pair, round to fp16 (or bf16), optionally split
 //     hi/lo, and store the 128 x 64 tile into shared memory in the canonical
 //     no-swizzle K-major UMMA layout (two A buffers);
 //   * 1 producer warp streams point tiles X_j (transposed, padded with far
@@ -164,9 +164,9 @@ __device__ __forceinline__ float mufu_ex2_neg(float x) {  // 2^-x
     asm("{\n .reg .f32 t;\n neg.f32 t, %1;\n ex2.approx.ftz.f32 %0, t;\n}" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ float mufu_rsqrt(float x) {
+__device__ __forceinline__ float mufu_sqrt(float x) {
     float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 
@@ -175,15 +175,13 @@ __device__ __forceinline__ float mufu_rsqrt(float x) {
 // so the exponential is a bare 2^-x:
 //   Matern: u' = u log2 e,  k = (1 + u' ln2 + u'^2 ln2^2 / 3) 2^-u'
 //   RBF:    u2' = u2 log2 e, k = 2^-u2'
-// u2 starts at 1e-30 so that rsqrt never sees 0.
 constexpr float LN2 = 0.69314718055994531f;
 constexpr float LN2SQ_3 = 0.16015100463940035f;  // (ln 2)^2 / 3
 
 template <int KIND>
 __device__ __forceinline__ float2 kval2(float2 u2) {
     if (KIND == LD_RBF) return make_float2(mufu_ex2_neg(u2.x), mufu_ex2_neg(u2.y));
-    const float2 rs = make_float2(mufu_rsqrt(u2.x), mufu_rsqrt(u2.y));
-    const float2 u = __fmul2_rn(u2, rs);
+    const float2 u = make_float2(mufu_sqrt(u2.x), mufu_sqrt(u2.y));
     const float2 e = make_float2(mufu_ex2_neg(u.x), mufu_ex2_neg(u.y));
     const float2 poly = __ffma2_rn(__ffma2_rn(u, make_float2(LN2SQ_3, LN2SQ_3), make_float2(LN2, LN2)), u,
                                    make_float2(1.f, 1.f));
@@ -230,8 +228,11 @@ __host__ __device__ inline Layout make_layout(int N, int d, int nprod, int sl) {
 
 template <int KIND, int DC, int NPROD, bool BF16, bool DRAIN>
 __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L) {
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte aligned base by pointer arithmetic on the shared array itself, so the
+    // compiler keeps shared-window loads and stores (an integer round trip would
+    // turn every access into a generic one)
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);  // [sl] loads landed
     uint64_t *empty = full + 8;                           // [sl] MMA done with load stage
     uint64_t *afull = empty + 8;                          // [sa] A tile written
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
         };
         const int C = (T + KCH - 1) / KCH;  // chunks
         int drained = 0;                     // chunks already drained
-        const float2 tiny = make_float2(1e-30f, 1e-30f);
+        const float2 zero2 = make_float2(0.f, 0.f);
         bool ok = true;
         for (int t = 0; t < T; ++t) {
             const int sl = t % SL, sa = t % SA;
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int jj = kq * 8 + 2 * q;
-                    float2 u0 = tiny, u1 = tiny;
+                    float2 u0 = zero2, u1 = zero2;
 #pragma unroll
                     for (int a = 0; a < 8; ++a) {
                         if (a < dd) {
