@@ -91,7 +91,8 @@ typedef struct {
                                 0: iterate until rel_tol */
     int32_t precision;       /* ld_precision */
     int32_t residual_check;  /* 1: fill ld_result.max_resid (one extra K V pass) */
-    int32_t reserved;
+    int32_t dense;           /* 1: materialise M = K + noise I once (n*n words in the
+                                workspace) and apply it from HBM; 0: matrix-free */
     uint64_t seed;           /* SplitMix64 seed of the probes when probes_dev is NULL */
     double rel_tol;          /* stop when max_i ||r_i|| / ||z_i|| < rel_tol (seed system) */
 } ld_options;
@@ -155,6 +156,15 @@ int ld_kz_static(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
 int ld_kz_dl(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
              const void *V_dev, void *W_dev, void *Wdl_dev, int32_t c,
              int32_t precision, void *stream);
+
+/* Stored dense variant of the same product: M = K + noise I written row-major
+ * n-by-n (float64 for LD_FP64, float32 otherwise; ld_dense_bytes(n, precision)
+ * bytes, caller-owned), then W = M V reading M once per product. */
+size_t ld_dense_bytes(int64_t n, int32_t precision);
+int ld_dense_materialize(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
+                         int32_t precision, void *M_dev, void *stream);
+int ld_dense_kz(const void *M_dev, int64_t n, const void *V_dev, void *W_dev, int32_t c,
+                int32_t precision, void *stream);
 
 /* Rademacher block from the SplitMix64 stream (Steele, Lea & Flood 2014):
  * Z[i, j] (row-major n-by-s int8) uses counter (col0 + j) * n + i and is +1
@@ -235,6 +245,11 @@ int logdet_grad(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
  * time (ms), the launch count, the kernel evaluations (n^2 per launch) and the
  * multiply-add flops (2 n^2 c per product) they did.  Single-threaded use. */
 int64_t ld_launch_count(void);
+/* Failure-detection self-test: one thread waits on an mbarrier that nothing
+ * completes, with the bounded wait the kernel product uses (budget in SM
+ * cycles, <= 4e9).  Returns LD_ERR_DEVICE_TIMEOUT once the budget runs out; the
+ * context stays usable.  Not part of the paper. */
+int ld_selftest_wait_timeout(int64_t budget_cycles, void *stream);
 int ld_profile_begin(void);
 int ld_profile_end(double *kz_ms, int64_t *kz_launches, double *kz_pairs, double *kz_mma_flops);
 

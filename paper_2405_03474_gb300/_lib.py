@@ -49,7 +49,7 @@ class LdKernel(ctypes.Structure):
 class LdOptions(ctypes.Structure):
     _fields_ = [("order", c_int32), ("num_probes", c_int32), ("probes_per_block", c_int32),
                 ("max_iters", c_int32), ("fixed_iters", c_int32), ("precision", c_int32),
-                ("residual_check", c_int32), ("reserved", c_int32), ("seed", c_uint64),
+                ("residual_check", c_int32), ("dense", c_int32), ("seed", c_uint64),
                 ("rel_tol", c_double)]
 
 
@@ -70,6 +70,9 @@ _SIGS = {
     "ld_kz_static_capacity": (c_size_t, []),
     "ld_kz_static": (c_int32, [_P, c_int64, c_int32, LdKernel, _P, _P, c_int32, c_int32, _P]),
     "ld_kz_dl": (c_int32, [_P, c_int64, c_int32, LdKernel, _P, _P, _P, c_int32, c_int32, _P]),
+    "ld_dense_bytes": (c_size_t, [c_int64, c_int32]),
+    "ld_dense_materialize": (c_int32, [_P, c_int64, c_int32, LdKernel, c_int32, _P, _P]),
+    "ld_dense_kz": (c_int32, [_P, c_int64, _P, _P, c_int32, c_int32, _P]),
     "ld_rademacher": (c_int32, [c_uint64, c_int64, c_int32, c_int32, _P, _P]),
     "precond_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int32]),
     "precond_build": (c_int32, [_P, c_int64, c_int32, LdKernel, c_int32, c_int32, c_uint64, c_int32,
@@ -83,6 +86,7 @@ _SIGS = {
     "logdet_estimate": (c_int32, [_P, c_int64, c_int32, LdKernel, _P, _P, _P, _P, _P, c_size_t, _P, _P]),
     "logdet_grad": (c_int32, [_P, c_int64, c_int32, LdKernel, _P, _P, _P, _P, c_size_t, _P, _P, _P]),
     "ld_launch_count": (c_int64, []),
+    "ld_selftest_wait_timeout": (c_int32, [c_int64, _P]),
     "ld_profile_begin": (c_int32, []),
     "ld_profile_end": (c_int32, [_P, _P, _P, _P]),
     "surrogate_create": (c_int32, [c_uint64, _P, _P]),

@@ -107,6 +107,27 @@ def ld_kz_dl(X, V, kernel, precision="fp32", stream=None):
     return W, Wdl
 
 
+def ld_dense_materialize(X, kernel, precision="fp32", stream=None):
+    """M = K(X, X) + noise I as a dense n-by-n tensor (float64 for fp64, else float32)."""
+    lib = _lib.load()
+    X = _points(X)
+    p = _prec(precision)
+    n, d = X.shape
+    M = torch.empty((n, n), dtype=torch.float64 if p == _lib.FP64 else torch.float32, device=X.device)
+    check(lib.ld_dense_materialize(_ptr(X), n, d, kernel.c(), p, _ptr(M), _stream(stream)), "ld_dense_materialize")
+    return M
+
+
+def ld_dense_kz(M, V, precision="fp32", stream=None):
+    """W = M V for a stored dense M."""
+    lib = _lib.load()
+    _need_cuda(M, V)
+    W = torch.empty_like(V)
+    check(lib.ld_dense_kz(_ptr(M), M.shape[0], _ptr(V), _ptr(W), V.shape[1], _prec(precision), _stream(stream)),
+          "ld_dense_kz")
+    return W
+
+
 def ld_rademacher(seed, n, s, col0=0, device="cuda", stream=None):
     """n-by-s int8 Rademacher block from SplitMix64(seed)."""
     lib = _lib.load()
@@ -189,9 +210,9 @@ class Precond:
 
 
 def make_options(order=3, num_probes=16, probes_per_block=None, max_iters=1000, fixed_iters=0,
-                 precision="fp32", residual_check=False, seed=1, rel_tol=1e-6):
+                 precision="fp32", residual_check=False, seed=1, rel_tol=1e-6, dense=False):
     return LdOptions(int(order), int(num_probes), int(probes_per_block or num_probes), int(max_iters),
-                     int(fixed_iters), _prec(precision), int(bool(residual_check)), 0, int(seed),
+                     int(fixed_iters), _prec(precision), int(bool(residual_check)), int(bool(dense)), int(seed),
                      float(rel_tol))
 
 

@@ -257,13 +257,15 @@ struct Bufs {
     // residual / gradient
     T *Xall, *Y, *W1, *W2;
     double *gdots;
+    T *M;  // stored dense M = K + noise I (dense mode), else null
 };
 
 // Carve (or measure) the estimator's scratch.
 template <typename T>
 void carve(Arena &a, Bufs<T> &b, int64_t n, int d, const ld_precond *P, int s, int m,
-           int max_iters, int precision, bool vectors, bool extra) {
+           int max_iters, int precision, bool vectors, bool extra, bool dense) {
     const size_t ns = (size_t)n * s;
+    b.M = dense ? a.take<T>((size_t)n * (size_t)n) : nullptr;
     const int sm = s * m;
     b.Xs = a.take<T>((size_t)n * d);
     b.Zi8 = a.take<int8_t>(ns);
@@ -308,12 +310,12 @@ void carve(Arena &a, Bufs<T> &b, int64_t n, int d, const ld_precond *P, int s, i
 // arena's remaining space and gives it back after each call)
 template <typename T>
 size_t run_bytes(int64_t n, int d, const ld_precond *P, int s, int m, int max_iters, int precision,
-                 bool vectors, bool extra) {
+                 bool vectors, bool extra, bool dense) {
     Arena meas;
     meas.measuring = true;
     Bufs<T> b;
-    carve<T>(meas, b, n, d, P, s, m, max_iters, precision, vectors, extra);
-    meas.take<char>(kz_any_workspace<T>(n, d, extra ? std::max(s, s * m) : s, precision));
+    carve<T>(meas, b, n, d, P, s, m, max_iters, precision, vectors, extra, dense);
+    if (!dense) meas.take<char>(kz_any_workspace<T>(n, d, extra ? std::max(s, s * m) : s, precision));
     return meas.off;
 }
 
@@ -322,12 +324,16 @@ template <typename T>
 int apply_B(const ld_precond *P, Bufs<T> &b, const T *Xs, int64_t n, int d, const ld_kernel &k,
             const T *V, T *out, T *tmp1, T *tmp2, int c, double shift, int precision, Arena &a,
             cudaStream_t st) {
+    auto product = [&](const T *in, T *o) -> int {
+        if (b.M) return dense_product<T>(b.M, n, in, o, c, st);
+        return kz_any<T>(Xs, n, d, k, in, o, c, precision, a, st);
+    };
     if (P) {
         LD_TRY(precond_apply_impl<T>(P, true, V, tmp1, c, b.Td, b.Tt, b.Ut, b.ppart, st));
-        LD_TRY(kz_any<T>(Xs, n, d, k, tmp1, tmp2, c, precision, a, st));
+        LD_TRY(product(tmp1, tmp2));
         LD_TRY(precond_apply_impl<T>(P, false, tmp2, out, c, b.Td, b.Tt, b.Ut, b.ppart, st));
     } else {
-        LD_TRY(kz_any<T>(Xs, n, d, k, V, out, c, precision, a, st));
+        LD_TRY(product(V, out));
     }
     if (shift != 0.0) LD_TRY(axpy<T>((int64_t)n * c, (T)shift, V, out, st));
     return LD_OK;
@@ -355,14 +361,16 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
     const int max_iters = o.fixed_iters > 0 ? std::min(o.fixed_iters, o.max_iters) : o.max_iters;
     Bufs<T> b;
     Arena a;
-    LD_TRY(arena_open(a, ws, ws_bytes, run_bytes<T>(n, d, P, s, m, max_iters, o.precision, vectors, vectors)));
+    const bool dense = o.dense != 0;
+    LD_TRY(arena_open(a, ws, ws_bytes, run_bytes<T>(n, d, P, s, m, max_iters, o.precision, vectors, vectors, dense)));
     int code = [&]() -> int {
-        carve<T>(a, b, n, d, P, s, m, max_iters, o.precision, vectors, vectors);
+        carve<T>(a, b, n, d, P, s, m, max_iters, o.precision, vectors, vectors, dense);
         if (a.overflow) {
             set_error("internal: estimator workspace overflow");
             return LD_ERR_WORKSPACE;
         }
         LD_TRY(prep_points<T>(X, n, d, point_scale(kern), b.Xs, st));
+        if (dense) LD_TRY(dense_materialize<T>(b.Xs, n, d, kern, b.M, st));
         const size_t ns = (size_t)n * s;
         const double smin = rk.sigma[0];
         Shifts sh;
@@ -492,6 +500,8 @@ int validate(const double *X, int64_t n, int d, const ld_kernel &k, const ld_pre
     LD_REQUIRE(o->fixed_iters >= 0, "fixed_iters must be >= 0");
     LD_REQUIRE(o->fixed_iters > 0 || o->rel_tol > 0, "rel_tol must be > 0 without fixed_iters");
     LD_REQUIRE(o->precision >= LD_FP64 && o->precision <= LD_F16X3_TC, "bad precision");
+    LD_REQUIRE(o->dense == 0 || o->dense == 1, "dense must be 0 or 1");
+    LD_REQUIRE(o->dense == 0 || n <= (int64_t)1 << 18, "dense mode keeps n*n words: n <= 262144");
     if (P) {
         LD_REQUIRE(P->n == n, "preconditioner built for n = %lld, not %lld", (long long)P->n, (long long)n);
         LD_REQUIRE((P->precision == LD_FP64) == (o->precision == LD_FP64),
@@ -540,8 +550,10 @@ size_t logdet_workspace_size(int64_t n, int32_t d, const ld_precond *P, const ld
     const int max_iters = opt->fixed_iters > 0 ? std::min(opt->fixed_iters, opt->max_iters) : opt->max_iters;
     const bool vectors = true;  // enough for residual check and gradient
     if (opt->precision == LD_FP64)
-        return run_bytes<double>(n, d, P, opt->probes_per_block, rk.m, max_iters, opt->precision, vectors, vectors);
-    return run_bytes<float>(n, d, P, opt->probes_per_block, rk.m, max_iters, opt->precision, vectors, vectors);
+        return run_bytes<double>(n, d, P, opt->probes_per_block, rk.m, max_iters, opt->precision, vectors, vectors,
+                                 opt->dense != 0);
+    return run_bytes<float>(n, d, P, opt->probes_per_block, rk.m, max_iters, opt->precision, vectors, vectors,
+                            opt->dense != 0);
 }
 
 int logdet_estimate(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, const ld_precond *P,

@@ -117,6 +117,12 @@ template <typename T>
 int kz_dl_simt(const T *Xs, int64_t n, int d, int kind, double lengthscale, double variance,
                const T *V, T *W, T *Wdl, int c, cudaStream_t st);
 
+// stored dense M = K + noise I (row-major n x n) and W = M V (dense_path.cu)
+template <typename T>
+int dense_materialize(const T *Xs, int64_t n, int d, const ld_kernel &k, T *M, cudaStream_t st);
+template <typename T>
+int dense_product(const T *M, int64_t n, const T *V, T *W, int c, cudaStream_t st);
+
 // tensor-core product (float vectors)
 size_t kz_tc_workspace(int64_t n, int d, int c, int precision);
 int kz_tc(const float *Xs, int64_t n, int d, int kind, double variance, double noise,

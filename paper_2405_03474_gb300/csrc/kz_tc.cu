@@ -352,23 +352,22 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
         }
     } else {
         // ---------------- eval warps: K tile into shared memory
-        const int e = threadIdx.x;          // 0 .. 255
-        const int rp = e & 63;              // rows rp and rp + 64
-        const int jq = e >> 6;              // j range [16 jq, 16 jq + 16)
+        // thread (lane, warp): rows lane + 32 k (k = 0..3), j in [8 warp, 8 warp + 8)
+        const int rg = lane;
+        const int kq = warp;                // core-matrix column (8 j values) of this warp
         const int quad = warp & 3;          // TMEM lane quadrant of this warp
         const int halfc = warp >> 2;        // column half handled in drains/epilogue
         const int ncol_half = p.N / 2;
-        // own coordinates, negated and duplicated into pairs: tiles 2*block and 2*block+1
-        float2 xr0[8], xr1[8];
-        {
-            const float *t0 = p.Xp + (size_t)(2 * blockIdx.x) * TJ * dd;
-            const float *t1 = t0 + (size_t)TJ * dd;
+        // own coordinates, negated and duplicated into pairs
+        float2 xr[4][8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int r = rg + 32 * k;
+            const float *tile = p.Xp + (size_t)(2 * blockIdx.x + (r >> 6)) * TJ * dd;
 #pragma unroll
             for (int a = 0; a < 8; ++a) {
-                const float v0 = a < dd ? -t0[a * TJ + rp] : 0.f;
-                const float v1 = a < dd ? -t1[a * TJ + rp] : 0.f;
-                xr0[a] = make_float2(v0, v0);
-                xr1[a] = make_float2(v1, v1);
+                const float v = a < dd ? -tile[a * TJ + (r & 63)] : 0.f;
+                xr[k][a] = make_float2(v, v);
             }
         }
         // move chunk k's TMEM buffer into the fp32 partial sums (round to nearest)
@@ -388,7 +387,6 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
         };
         const int C = (T + KCH - 1) / KCH;  // chunks
         int drained = 0;                     // chunks already drained
-        const float2 zero2 = make_float2(0.f, 0.f);
         bool ok = true;
         for (int t = 0; t < T; ++t) {
             const int sl = t % SL, sa = t % SA;
@@ -406,46 +404,48 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
             }
             uint8_t *ast = abase + (size_t)sa * L.a_bytes;
             const float *xs = reinterpret_cast<const float *>(lbase + (size_t)sl * L.l_bytes + L.b_bytes);
+            // the 8 points j of this warp, per coordinate (two 16-byte broadcast loads each)
+            float2 xj[8][4];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int kq = jq * 2 + h;  // core-matrix column (8 j values)
-                uint32_t w0[4], w1[4];       // 8 halves per row
-                float2 f0[4], f1[4];
+            for (int a = 0; a < 8; ++a) {
+                if (a < dd) {
+                    const float4 lo4 = *reinterpret_cast<const float4 *>(xs + a * TJ + kq * 8);
+                    const float4 hi4 = *reinterpret_cast<const float4 *>(xs + a * TJ + kq * 8 + 4);
+                    xj[a][0] = make_float2(lo4.x, lo4.y);
+                    xj[a][1] = make_float2(lo4.z, lo4.w);
+                    xj[a][2] = make_float2(hi4.x, hi4.y);
+                    xj[a][3] = make_float2(hi4.z, hi4.w);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t w[4];
+                float2 f[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int jj = kq * 8 + 2 * q;
-                    float2 u0 = zero2, u1 = zero2;
+                    float2 u = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int a = 0; a < 8; ++a) {
                         if (a < dd) {
-                            const float2 xj = *reinterpret_cast<const float2 *>(xs + a * TJ + jj);
-                            const float2 d0 = __fadd2_rn(xj, xr0[a]), d1 = __fadd2_rn(xj, xr1[a]);
-                            u0 = __ffma2_rn(d0, d0, u0);
-                            u1 = __ffma2_rn(d1, d1, u1);
+                            const float2 dv = __fadd2_rn(xj[a][q], xr[k][a]);
+                            u = __ffma2_rn(dv, dv, u);
                         }
                     }
-                    f0[q] = kval2<KIND>(u0);
-                    f1[q] = kval2<KIND>(u1);
-                    w0[q] = pack2<BF16>(f0[q].x, f0[q].y);
-                    w1[q] = pack2<BF16>(f1[q].x, f1[q].y);
+                    f[q] = kval2<KIND>(u);
+                    w[q] = pack2<BF16>(f[q].x, f[q].y);
                 }
-                const int r0i = rp, r1i = rp + 64;
-                const size_t off0 = (size_t)(r0i >> 3) * 1024 + (size_t)kq * 128 + (size_t)(r0i & 7) * 16;
-                const size_t off1 = (size_t)(r1i >> 3) * 1024 + (size_t)kq * 128 + (size_t)(r1i & 7) * 16;
-                *reinterpret_cast<uint4 *>(ast + off0) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-                *reinterpret_cast<uint4 *>(ast + off1) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+                const int r = rg + 32 * k;
+                const size_t off = (size_t)(r >> 3) * 1024 + (size_t)kq * 128 + (size_t)(r & 7) * 16;
+                *reinterpret_cast<uint4 *>(ast + off) = make_uint4(w[0], w[1], w[2], w[3]);
                 if (NPROD == 3) {
-                    uint32_t l0[4], l1[4];
                     const float2 m1 = make_float2(-1.f, -1.f);
+                    uint32_t l[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float2 r0 = __ffma2_rn(unpack2<BF16>(w0[q]), m1, f0[q]);  // k - hi
-                        const float2 r1 = __ffma2_rn(unpack2<BF16>(w1[q]), m1, f1[q]);
-                        l0[q] = pack2<BF16>(r0.x, r0.y);
-                        l1[q] = pack2<BF16>(r1.x, r1.y);
+                        const float2 rq = __ffma2_rn(unpack2<BF16>(w[q]), m1, f[q]);  // k - hi
+                        l[q] = pack2<BF16>(rq.x, rq.y);
                     }
-                    *reinterpret_cast<uint4 *>(ast + A_BYTES + off0) = make_uint4(l0[0], l0[1], l0[2], l0[3]);
-                    *reinterpret_cast<uint4 *>(ast + A_BYTES + off1) = make_uint4(l1[0], l1[1], l1[2], l1[3]);
+                    *reinterpret_cast<uint4 *>(ast + A_BYTES + off) = make_uint4(l[0], l[1], l[2], l[3]);
                 }
             }
             fence_async_smem();
@@ -744,4 +744,53 @@ int kz_tc(const float *Xs, int64_t n, int d, int kind, double variance, double n
     return code;
 }
 
+namespace {
+// A wait that nothing completes: one thread waits on an mbarrier no one arrives at,
+// with the same bounded wait the kernel product uses but a caller-chosen budget.
+__global__ void wait_timeout_selftest_kernel(long long budget, int *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        long long t0 = clock64();
+        bool ok = false;
+        while (!(ok = mbar_try_wait(&bar, 0))) {
+            if (clock64() - t0 > budget) break;
+        }
+        *err = ok ? 0 : ERR_TIMEOUT;
+    }
+}
+}  // namespace
+
 }  // namespace ld
+
+extern "C" int ld_selftest_wait_timeout(int64_t budget_cycles, void *stream) {
+    ld::clear_error();
+    if (budget_cycles < 0 || budget_cycles > 4000000000ll) {
+        ld::set_error("ld_selftest_wait_timeout: budget must be in [0, 4e9] cycles");
+        return LD_ERR_INVALID;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int *d_err = nullptr;
+    LD_CHECK_CUDA(cudaMalloc(&d_err, sizeof(int)));
+    int herr = -1;
+    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        ld::wait_timeout_selftest_kernel<<<1, 32, 0, st>>>(budget_cycles, d_err);
+        e = cudaGetLastError();
+        ld::count_launches(1);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_err);
+    if (e != cudaSuccess) {
+        ld::set_error("ld_selftest_wait_timeout: %s", cudaGetErrorString(e));
+        return LD_ERR_CUDA;
+    }
+    if (herr) {
+        ld::set_error("device-side wait gave up after %lld cycles (as intended by the self-test)",
+                      (long long)budget_cycles);
+        return LD_ERR_DEVICE_TIMEOUT;
+    }
+    return LD_OK;
+}
