@@ -119,21 +119,61 @@ class HyperSurrogate:
         return err, err <= tol
 
 
+def train_and_evaluate(est, thetas, labels, held_out=64, queries=65536, epochs=800, batch=128, lr=2e-3, seed=0):
+    """Fit on labels, then report what the network gains: error against fresh
+    estimator values on held-out hyperparameters, time per query of batched
+    inference against time per estimate, and an audit."""
+    hs = HyperSurrogate(est, seed=seed)
+    t0 = time.perf_counter()
+    loss = hs.fit(thetas, labels, epochs=epochs, batch=batch, lr=lr)
+    t_fit = time.perf_counter() - t0
+    test = inputs.sobol_theta(held_out, seed=101)
+    t0 = time.perf_counter()
+    ref = np.array([est(t) for t in test])
+    t_est = (time.perf_counter() - t0) / held_out
+    pred, _ = hs.predict(test)
+    q = inputs.sobol_theta(queries, seed=202)
+    hs.predict(q, want_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs.predict(q, want_grad=True)
+    torch.cuda.synchronize()
+    t_q = (time.perf_counter() - t0) / queries
+    err = np.abs(pred - ref)
+    return {"labels": int(len(labels)), "train_loss_normalised": loss, "fit_s": t_fit,
+            "held_out": held_out, "max_abs_err_logdet_per_n": float(err.max()),
+            "mean_abs_err_logdet_per_n": float(err.mean()),
+            "max_rel_err_logdet": float(np.max(err / np.abs(ref))),
+            "label_spread": float(np.max(labels) - np.min(labels)),
+            "estimator_s_per_query": t_est, "surrogate_s_per_query_with_grad": t_q,
+            "speedup_per_query": t_est / t_q, "queries": queries}
+
+
 def main():
-    ap = argparse.ArgumentParser(description="label job of the surrogate workload (checkpointed)")
+    ap = argparse.ArgumentParser(description="label job of the surrogate workload (checkpointed), "
+                                             "then training and evaluation")
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--checkpoint", default="surrogate_labels.npz")
     ap.add_argument("--rank", type=int, default=None)
+    ap.add_argument("--power-iters", type=int, default=None)
     ap.add_argument("--t", type=int, default=20)
+    ap.add_argument("--train", action="store_true", help="train and evaluate after labelling")
     args = ap.parse_args()
     w = inputs.WORKLOADS["surrogate_matern_n262144_d3"]
     n = args.n or w["n"]
     X = torch.as_tensor(inputs.points(n, w["d"], "uniform", seed=inputs.SEED_POINTS)).cuda()
-    est = Estimator(X, w["kind"], rank=args.rank or w["rank"], power_iters=w["power_iters"], probes=w["probes"],
-                    t=args.t)
+    est = Estimator(X, w["kind"], rank=args.rank or w["rank"],
+                    power_iters=w["power_iters"] if args.power_iters is None else args.power_iters,
+                    probes=w["probes"], t=args.t)
     thetas = inputs.sobol_theta(args.count, seed=0)
-    generate_labels(est, thetas, checkpoint=args.checkpoint, log=print)
+    labels = generate_labels(est, thetas, checkpoint=args.checkpoint, log=print)
+    if args.train:
+        import json
+        out = train_and_evaluate(est, thetas, labels)
+        out.update({"n": n, "rank": est.rank, "power_iters": est.power_iters, "t": args.t,
+                    "probes": w["probes"]})
+        print(json.dumps(out))
 
 
 if __name__ == "__main__":
