@@ -126,6 +126,22 @@ def estimate_lanczos(B, logdet_P, Z, k, t):
     return est, per_probe, q
 
 
+def estimate_slq(B, logdet_P, Z, t):
+    """Stochastic Lanczos quadrature (Ubaru, Chen & Saad 2017), the comparison
+    method of Section 3: t Lanczos steps per probe, T = V diag(theta) V^T,
+    z^T log(B) z ~ |z|^2 sum_k (e_1^T v_k)^2 log(theta_k).  Returns the estimate
+    log det P + (1/s) sum_i of those forms, and the per-probe forms."""
+    Z = np.asarray(Z, dtype=np.float64)
+    per = np.empty(Z.shape[1])
+    for i in range(Z.shape[1]):
+        v = Z[:, i]
+        a, bt, _ = lanczos(B, v, t)
+        T = np.diag(a) + np.diag(bt, 1) + np.diag(bt, -1)
+        theta, V = np.linalg.eigh(T)
+        per[i] = float(v @ v) * float(np.sum(V[0] ** 2 * np.log(theta)))
+    return float(logdet_P + np.mean(per)), per
+
+
 def rk_bias(B, k):
     """Exact r_k bias of the trace term: sum_i [log lam_i(B) - r_k(lam_i(B))]."""
     lam = np.linalg.eigvalsh(B)

@@ -69,6 +69,12 @@ def build(M, Omega, q, noise):
     return A, D
 
 
+def build_scaled(M, Omega, q, a):
+    """Appendix "Truncated Randomized SVD plus scaling": P = a I + A A^T."""
+    A = rsvd(lambda V: M @ V, Omega, q)
+    return A, np.full(M.shape[0], float(a))
+
+
 def factors(A, D):
     """Split factor of P = D + A A^T (see module docstring).
 

@@ -44,3 +44,21 @@ def rademacher_block(seed, n, s, col0=0):
     k = cols[None, :] * np.uint64(n) + rows[:, None]
     bits = splitmix64(seed, k) >> np.uint64(63)
     return 1.0 - 2.0 * bits.astype(np.float64)
+
+
+def uniform_open(seed, counters):
+    """(0, 1) uniforms from the top 53 bits of the SplitMix64 outputs: (m + 0.5) 2^-53."""
+    m = splitmix64(seed, counters) >> np.uint64(11)
+    return (m.astype(np.float64) + 0.5) * 2.0 ** -53
+
+
+def gaussian_block(seed, n, s, col0=0):
+    """n-by-s N(0, 1) block by the Box-Muller transform (Box & Muller 1958): entry
+    (i, c) uses the uniforms of counters 2k and 2k + 1, k = (col0 + c) n + i, and is
+    sqrt(-2 ln u1) cos(2 pi u2)."""
+    cols = np.arange(col0, col0 + s, dtype=np.uint64)
+    rows = np.arange(n, dtype=np.uint64)
+    k = cols[None, :] * np.uint64(n) + rows[:, None]
+    u1 = uniform_open(seed, np.uint64(2) * k)
+    u2 = uniform_open(seed, np.uint64(2) * k + np.uint64(1))
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)

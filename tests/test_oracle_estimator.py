@@ -118,3 +118,25 @@ def test_r3_more_accurate_than_r1_on_kernel_matrices():
         B = precond.operator_B(M, precond.factors(A, D))
         b1, b3, b5 = (abs(estimator.rk_bias(B, k)) for k in (1, 3, 5))
         assert b3 < b1 and b5 < b1
+
+
+def test_slq_with_full_lanczos_is_exact_quadratic_form():
+    # With t = n the Gauss quadrature of z^T log(B) z is exact: compare with eigh(B).
+    n = 40
+    X = inputs.points(n, 2, "uniform", seed=12)
+    M = kernels.kernel_matrix(X, kernels.MATERN52, 0.3, 1.0, 5e-2)
+    F = precond.factors(*precond.build(M, rademacher_block(2, n, 8), 2, 5e-2))
+    B = precond.operator_B(M, F)
+    lam, U = np.linalg.eigh(B)
+    Z = rademacher_block(3, n, 5)
+    _, per = estimator.estimate_slq(B, F["logdet_P"], Z, n)
+    ref = np.einsum("ij,i,ij->j", U.T @ Z, np.log(lam), U.T @ Z)
+    np.testing.assert_allclose(per, ref, rtol=1e-9)
+    # and with all 2^n sign vectors (n small) it gives log det M exactly
+    n2 = 8
+    X2 = inputs.points(n2, 2, "uniform", seed=13)
+    M2 = kernels.kernel_matrix(X2, kernels.RBF, 0.5, 1.0, 0.1)
+    F2 = precond.factors(*precond.identity(n2))
+    Zall = np.array(list(itertools.product([-1.0, 1.0], repeat=n2))).T
+    est, _ = estimator.estimate_slq(precond.operator_B(M2, F2), 0.0, Zall, n2)
+    assert est == pytest.approx(estimator.logdet_exact(M2), rel=1e-10)

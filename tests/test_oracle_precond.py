@@ -86,3 +86,17 @@ def test_identity_and_diagonal_preconditioners():
     d = np.array([1.0, 2.0, 4.0])
     A, D = precond.diagonal(d)
     assert precond.factors(A, D)["logdet_P"] == pytest.approx(np.log(8.0))
+
+
+def test_plus_scaling_variant():
+    # P = a I + A A^T keeps the rSVD factor and replaces the diagonal by a constant
+    n, r, a = 200, 12, 0.05
+    X = inputs.points(n, 2, "uniform", seed=8)
+    M = kernels.kernel_matrix(X, kernels.RBF, 0.4, 1.0, a)
+    Om = rademacher_block(2, n, r)
+    A1, _ = precond.build(M, Om, 2, a)
+    A2, D2 = precond.build_scaled(M, Om, 2, a)
+    np.testing.assert_allclose(A1 @ A1.T, A2 @ A2.T, atol=1e-12)
+    np.testing.assert_array_equal(D2, np.full(n, a))
+    F = precond.factors(A2, D2)
+    assert F["logdet_P"] == pytest.approx(np.linalg.slogdet(a * np.eye(n) + A2 @ A2.T)[1], rel=1e-12)

@@ -40,3 +40,19 @@ def test_rademacher_block_layout_and_balance():
     np.testing.assert_array_equal(Z2, Z[:, 4:7])
     big = splitmix.rademacher_block(7, 200000, 1)
     assert abs(big.mean()) < 0.01
+
+
+def test_gaussian_block_is_standard_normal():
+    from scipy import stats
+    Z = splitmix.gaussian_block(9, 200000, 2)
+    assert Z.shape == (200000, 2)
+    # Kolmogorov-Smirnov against N(0, 1) and the first two moments
+    assert stats.kstest(Z[:, 0], "norm").pvalue > 1e-3
+    assert abs(Z.mean()) < 0.01 and abs(Z.var() - 1.0) < 0.01
+    # entry (i, c) is Box-Muller of counters 2k, 2k+1 with k = c n + i
+    n = 200000
+    k = 1 * n + 123
+    u1 = (float(int(splitmix.splitmix64(9, [2 * k])[0]) >> 11) + 0.5) * 2.0 ** -53
+    u2 = (float(int(splitmix.splitmix64(9, [2 * k + 1])[0]) >> 11) + 0.5) * 2.0 ** -53
+    import math
+    assert Z[123, 1] == math.sqrt(-2 * math.log(u1)) * math.cos(2 * math.pi * u2)
