@@ -1,0 +1,639 @@
+// Symmetric tensor-core kernel product W = (K + noise I) V for up to 16 columns
+// (the CG passes: one column per probe), evaluating each kernel value once.
+//
+// K is symmetric, so the 128 x 128 block K_IJ serves two products: W_I += K_IJ V_J
+// and W_J += K_IJ^T V_I.  The CTA owning row block I visits the blocks
+// J = (I + b) mod NB, b = 0 .. NB/2 (for even NB the block at distance NB/2 goes
+// to the smaller I only), so every unordered pair of blocks is evaluated once and
+// the work per CTA is balanced.  Per block:
+//   * 16 eval warps evaluate the 128 x 128 tile into shared memory (packed f32x2
+//     differences and polynomial, one MUFU sqrt + ex2 per pair, fp16 hi/lo);
+//   * the MMA thread issues D_I += K_IJ V_J (K-major A: rows i, K = j) and
+//     D'_J = K_IJ^T V_I (the same shared tile read as an MN-major A: rows j, K = i);
+//   * two blocks later the eval warps read D'_J from tensor memory, stage it in
+//     shared memory and add it into W_J with one cp.reduce.async.bulk .add.f32.
+// W is zeroed first and every contribution (including the owner's own rows and
+// the noise term, at the end) is added, so the order of additions across CTAs is
+// the only run-to-run difference (fp32 rounding).  D_I is accumulated in tensor
+// memory in chunks of 4 blocks and drained to fp32 round-to-nearest partial
+// sums, as in the non-symmetric kernel.  Every mbarrier wait is bounded.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "tc_common.cuh"
+
+namespace ld {
+
+using namespace tc;
+
+namespace {
+
+constexpr int BR = 128;                     // block rows and block columns
+constexpr int SNEVAL = 16;                  // eval warps
+constexpr int SNTHREADS = (SNEVAL + 2) * 32;
+constexpr int HALF_TILE = BR * BR * 2;      // one 128 x 128 tile of halves (32 KB)
+constexpr int SKCH = 4;                     // blocks per TMEM chunk before a drain (hi/lo)
+constexpr int SYM_N = 16;                   // MMA N (columns, padded)
+constexpr int CORE_SBO = (BR / 8) * 128;    // 2048: byte step between 8-row groups
+
+struct SymParams {
+    const float *Xp;     // per 128-point tile: d x 128 floats, far-padded, log2 e folded in
+    const uint8_t *img;  // per 128-point tile: nprod x (16 x 128) halves, canonical K-major
+    const float *V;      // n x c
+    const float *colinv; // 1 / column scale (16)
+    float *W;            // zeroed; every contribution is added
+    int64_t n;
+    int d, c, NB, ncols_tmem, bulk_ok;
+    float variance, noise;
+    int *err;
+};
+
+struct SymLayout {
+    int sl, a_bytes, b_bytes, x_bytes, l_bytes, st_bytes;
+    int a_off, l_off, vi_off, st_off, acc_off, total;
+};
+
+SymLayout make_sym_layout(int d, int nprod, int c, int sl) {
+    SymLayout L;
+    L.sl = sl;
+    L.a_bytes = (nprod == 3 ? 2 : 1) * HALF_TILE;
+    L.b_bytes = (nprod == 3 ? 2 : 1) * SYM_N * BR * 2;
+    L.x_bytes = BR * d * 4;
+    L.l_bytes = ((L.b_bytes + L.x_bytes + 1023) / 1024) * 1024;
+    L.st_bytes = ((BR * c * 4 + 1023) / 1024) * 1024;
+    L.a_off = 1024;
+    L.l_off = L.a_off + 2 * L.a_bytes;
+    L.vi_off = L.l_off + sl * L.l_bytes;
+    L.st_off = L.vi_off + ((L.b_bytes + 1023) / 1024) * 1024;
+    L.acc_off = L.st_off + 2 * L.st_bytes;
+    const int acc = nprod == 3 ? BR * (SYM_N + 1) * 4 : 0;
+    L.total = L.acc_off + acc + 1024;
+    return L;
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void eval_barrier() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+
+template <int KIND, int DC, int NPROD, bool BF16>
+__global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLayout L) {
+    constexpr bool DRAIN = NPROD == 3;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);  // [sl]
+    uint64_t *empty = full + 8;                           // [sl]
+    uint64_t *afull = empty + 8;                          // [2]
+    uint64_t *aempty = afull + 2;                         // [2]
+    uint64_t *vfull = aempty + 2;                         // own V image landed
+    uint64_t *done = vfull + 1;
+    uint64_t *cfull = done + 1;                           // [2] D chunk in TMEM
+    uint64_t *cempty = cfull + 2;                         // [2] D chunk drained
+    uint64_t *tfull = cempty + 2;                         // [2] D' of a block in TMEM
+    uint64_t *tempty = tfull + 2;                         // [2] D' drained
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    int *s_err = reinterpret_cast<int *>(tmem_slot + 1);
+    uint8_t *abase = smem + L.a_off;
+    uint8_t *lbase = smem + L.l_off;
+    uint8_t *vimg = smem + L.vi_off;
+    float *stage_f = reinterpret_cast<float *>(smem + L.st_off);
+    float *sacc = reinterpret_cast<float *>(smem + L.acc_off);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int dd = DC > 0 ? DC : p.d;
+    const int I = blockIdx.x;
+    const int NB = p.NB, H = NB / 2;
+    const int T = (NB & 1) ? H + 1 : (I < H ? H + 1 : H);  // blocks J = (I + b) % NB
+    const int SL = L.sl;
+    const int N = SYM_N;
+    const uint32_t doff = DRAIN ? 2 * N : N;  // TMEM columns of the two D' buffers
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SL; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&afull[s], SNEVAL * 32);
+            mbar_init(&aempty[s], 1);
+            mbar_init(&cfull[s], 1);
+            mbar_init(&cempty[s], SNEVAL * 32);
+            mbar_init(&tfull[s], 1);
+            mbar_init(&tempty[s], SNEVAL * 32);
+        }
+        mbar_init(vfull, 1);
+        mbar_init(done, 1);
+        *s_err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_async_smem();
+    }
+    if (DRAIN)
+        for (int e = threadIdx.x; e < BR * (N + 1); e += SNTHREADS) sacc[e] = 0.f;
+    if (warp == SNEVAL) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(p.ncols_tmem)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == SNEVAL + 1) {
+        // ---------------- producer
+        if (lane == 0) {
+            const uint32_t xb = (uint32_t)(BR * dd * 4);
+            const uint32_t bb = (uint32_t)L.b_bytes;
+            mbar_expect_tx(vfull, bb);
+            bulk_g2s(vimg, p.img + (size_t)I * bb, bb, vfull);
+            int b = 0;
+            for (; b < T; ++b) {
+                const int J = (I + b) % NB;
+                const int s = b % SL;
+                if (b >= SL && !mbar_wait(&empty[s], ((b / SL) - 1) & 1)) {
+                    atomicOr(s_err, ERR_TIMEOUT);
+                    break;
+                }
+                uint8_t *st = lbase + (size_t)s * L.l_bytes;
+                mbar_expect_tx(&full[s], xb + bb);
+                bulk_g2s(st, p.img + (size_t)J * bb, bb, &full[s]);
+                bulk_g2s(st + L.b_bytes, p.Xp + (size_t)J * BR * dd, xb, &full[s]);
+            }
+            for (int u = std::max(0, b - SL); u < b; ++u)
+                if (!mbar_wait(&full[u % SL], (u / SL) & 1)) atomicOr(s_err, ERR_TIMEOUT);
+            if (!mbar_wait(vfull, 0)) atomicOr(s_err, ERR_TIMEOUT);
+        }
+    } else if (warp == SNEVAL) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc(BR, N, BF16 ? 1u : 0u, 0u);
+            const uint32_t idesc_t = make_idesc(BR, N, BF16 ? 1u : 0u, 1u);  // A read MN-major
+            const uint32_t bhalf = (uint32_t)(N * BR * 2);
+            bool ok = mbar_wait(vfull, 0);
+            const uint32_t vi0 = smem_u32(vimg);
+            for (int b = 0; b < T && ok; ++b) {
+                const int s = b % SL, sa = b & 1;
+                const int k = b / SKCH;
+                const bool first = DRAIN ? (b % SKCH == 0) : (b == 0);
+                const uint32_t dt = tmem + (DRAIN ? (uint32_t)((k & 1) * N) : 0u);
+                if (DRAIN && first && k >= 2 && !mbar_wait(&cempty[k & 1], ((k - 2) >> 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                if (b >= 3 && !mbar_wait(&tempty[b & 1], ((b - 3) >> 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                if (!mbar_wait(&afull[sa], (b >> 1) & 1) || !mbar_wait(&full[s], (b / SL) & 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(abase + (size_t)sa * L.a_bytes);
+                const uint32_t b0 = smem_u32(lbase + (size_t)s * L.l_bytes);
+                // D_I += K_IJ V_J: A K-major (lbo = 128 along j, sbo = 2048 along i)
+#pragma unroll
+                for (int ks = 0; ks < BR / 16; ++ks) {
+                    const uint32_t koff = (uint32_t)ks * 256u;
+                    const uint64_t ah = make_desc(a0 + koff, 128, CORE_SBO);
+                    const uint64_t bh = make_desc(b0 + koff, 128, CORE_SBO);
+                    mma_f16(dt, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
+                    if (NPROD == 3) {
+                        const uint64_t al = make_desc(a0 + (uint32_t)HALF_TILE + koff, 128, CORE_SBO);
+                        const uint64_t bl = make_desc(b0 + bhalf + koff, 128, CORE_SBO);
+                        mma_f16(dt, ah, bl, idesc, 1u);
+                        mma_f16(dt, al, bh, idesc, 1u);
+                    }
+                }
+                if (b >= 1) {
+                    // D'_J = K_IJ^T V_I: the same tile MN-major (rows j; lbo = 2048 along i,
+                    // sbo = 128 along j), B = own V image (K = i)
+                    const uint32_t tdt = tmem + doff + (uint32_t)((b & 1) * N);
+#pragma unroll
+                    for (int ks = 0; ks < BR / 16; ++ks) {
+                        const uint32_t koff_t = (uint32_t)ks * (2u * CORE_SBO);
+                        const uint32_t bkoff = (uint32_t)ks * 256u;
+                        const uint64_t ah = make_desc(a0 + koff_t, CORE_SBO, 128);
+                        const uint64_t bh = make_desc(vi0 + bkoff, 128, CORE_SBO);
+                        mma_f16(tdt, ah, bh, idesc_t, ks == 0 ? 0u : 1u);
+                        if (NPROD == 3) {
+                            const uint64_t al = make_desc(a0 + (uint32_t)HALF_TILE + koff_t, CORE_SBO, 128);
+                            const uint64_t bl = make_desc(vi0 + bhalf + bkoff, 128, CORE_SBO);
+                            mma_f16(tdt, ah, bl, idesc_t, 1u);
+                            mma_f16(tdt, al, bh, idesc_t, 1u);
+                        }
+                    }
+                    mma_commit(&tfull[b & 1]);
+                }
+                mma_commit(&empty[s]);
+                mma_commit(&aempty[sa]);
+                if (DRAIN && (b % SKCH == SKCH - 1 || b == T - 1)) mma_commit(&cfull[k & 1]);
+            }
+            if (!ok) atomicOr(s_err, ERR_TIMEOUT);
+            mma_commit(done);
+            // every issued MMA has finished before tensor memory is released below
+            if (!mbar_wait(done, 0)) atomicOr(s_err, ERR_TIMEOUT);
+        }
+    } else {
+        // ---------------- eval warps: rows lane + 32 k (k = 0..3), j in [8 warp, 8 warp + 8)
+        const int rg = lane;
+        const int kq = warp;
+        const int quad = warp & 3;       // TMEM lane quadrant
+        const int part = warp >> 2;      // 4 columns of the 16 in drains / epilogue
+        const int c4 = part * 4;
+        const int row = quad * 32 + lane;
+        float2 xr[4][8];
+        {
+            const float *tile = p.Xp + (size_t)I * BR * dd;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    const float v = a < dd ? -tile[a * BR + rg + 32 * k] : 0.f;
+                    xr[k][a] = make_float2(v, v);
+                }
+        }
+        float cscale[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cscale[q] = p.variance * p.colinv[c4 + q];
+
+        // Waits of the eval threads never leave the loop: after the first timeout (error
+        // word set) every later wait is skipped, so all 512 threads keep running the
+        // same sequence of named barriers and finish quickly.
+        auto wait_ok = [&](uint64_t *bar, uint32_t parity) {
+            if (*reinterpret_cast<volatile int *>(s_err)) return;
+            if (!mbar_wait(bar, parity)) atomicOr(s_err, ERR_TIMEOUT);
+        };
+        // D chunk k -> fp32 partial sums
+        auto drain_d = [&](int k) {
+            wait_ok(&cfull[k & 1], (k >> 1) & 1);
+            tc_fence_after();
+            float v[4];
+            tmem_ld4(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((k & 1) * N + c4), v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sacc[row * (N + 1) + c4 + q] += v[q];
+            tc_fence_before();
+            mbar_arrive(&cempty[k & 1]);
+        };
+        // D' of block bb -> W rows of block J = (I + bb) % NB (added)
+        auto drain_t = [&](int bb) {
+            if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            wait_ok(&tfull[bb & 1], ((bb - 1) >> 1) & 1);
+            tc_fence_after();
+            float v[4];
+            tmem_ld4(tmem + ((uint32_t)(quad * 32) << 16) + doff + (uint32_t)((bb & 1) * N + c4), v);
+            tc_fence_before();
+            mbar_arrive(&tempty[bb & 1]);
+            const int J = (I + bb) % NB;
+            const int64_t r0 = (int64_t)J * BR;
+            const int rows_valid = (int)std::min<int64_t>(BR, p.n - r0);
+            if (p.bulk_ok && rows_valid == BR) {  // uniform over the eval threads
+                float *stg = stage_f + (size_t)(bb & 1) * (L.st_bytes / 4);
+                eval_barrier();  // staging free: thread 0 waited for the last bulk read above
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c4 + q < p.c) stg[row * p.c + c4 + q] = v[q] * cscale[q];
+                fence_async_smem();
+                eval_barrier();
+                if (threadIdx.x == 0 && !*reinterpret_cast<volatile int *>(s_err)) {
+                    asm volatile(
+                        "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
+                            p.W + r0 * p.c),
+                        "r"(smem_u32(stg)), "r"((uint32_t)(BR * p.c * 4))
+                        : "memory");
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
+            } else if (row < rows_valid) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c4 + q < p.c) atomicAdd(p.W + (r0 + row) * p.c + c4 + q, v[q] * cscale[q]);
+            }
+        };
+
+        const int C = (T + SKCH - 1) / SKCH;
+        int drained = 0;
+        for (int b = 0; b < T; ++b) {
+            const int s = b % SL, sa = b & 1;
+            if (DRAIN && b % SKCH == SKCH / 2 && b >= SKCH + SKCH / 2) drain_d(drained++);
+            if (b >= 3) drain_t(b - 2);
+            wait_ok(&full[s], (b / SL) & 1);
+            if (b >= 2) wait_ok(&aempty[sa], ((b >> 1) - 1) & 1);
+            uint8_t *ast = abase + (size_t)sa * L.a_bytes;
+            const float *xs = reinterpret_cast<const float *>(lbase + (size_t)s * L.l_bytes + L.b_bytes);
+            float2 xj[8][4];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                if (a < dd) {
+                    const float4 lo4 = *reinterpret_cast<const float4 *>(xs + a * BR + kq * 8);
+                    const float4 hi4 = *reinterpret_cast<const float4 *>(xs + a * BR + kq * 8 + 4);
+                    xj[a][0] = make_float2(lo4.x, lo4.y);
+                    xj[a][1] = make_float2(lo4.z, lo4.w);
+                    xj[a][2] = make_float2(hi4.x, hi4.y);
+                    xj[a][3] = make_float2(hi4.z, hi4.w);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t w[4];
+                float2 f[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float2 u = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) {
+                        if (a < dd) {
+                            const float2 dv = __fadd2_rn(xj[a][q], xr[k][a]);
+                            u = __ffma2_rn(dv, dv, u);
+                        }
+                    }
+                    f[q] = kval2<KIND>(u);
+                    w[q] = pack2<BF16>(f[q].x, f[q].y);
+                }
+                const int r = rg + 32 * k;
+                const size_t off = (size_t)(r >> 3) * CORE_SBO + (size_t)kq * 128 + (size_t)(r & 7) * 16;
+                *reinterpret_cast<uint4 *>(ast + off) = make_uint4(w[0], w[1], w[2], w[3]);
+                if (NPROD == 3) {
+                    const float2 m1 = make_float2(-1.f, -1.f);
+                    uint32_t l[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 rq = __ffma2_rn(unpack2<BF16>(w[q]), m1, f[q]);
+                        l[q] = pack2<BF16>(rq.x, rq.y);
+                    }
+                    *reinterpret_cast<uint4 *>(ast + HALF_TILE + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                }
+            }
+            fence_async_smem();
+            mbar_arrive(&afull[sa]);
+        }
+        // ---------------- tail: remaining transposed blocks, D chunks, own rows
+        wait_ok(done, 0);
+        tc_fence_after();
+        for (int bb = std::max(1, T - 2); bb < T; ++bb) drain_t(bb);
+        if (DRAIN)
+            for (; drained < C; ++drained) drain_d(drained);
+        {
+            float v[4];
+            if (DRAIN) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = sacc[row * (N + 1) + c4 + q];
+            } else {
+                tmem_ld4(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c4, v);
+            }
+            const int64_t r0 = (int64_t)I * BR;
+            const int rows_valid = (int)std::min<int64_t>(BR, p.n - r0);
+            float outv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int col = c4 + q;
+                outv[q] = (row < rows_valid && col < p.c)
+                              ? v[q] * cscale[q] + p.noise * p.V[(r0 + row) * p.c + col]
+                              : 0.f;
+            }
+            if (p.bulk_ok && rows_valid == BR) {
+                if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                eval_barrier();
+                float *stg = stage_f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c4 + q < p.c) stg[row * p.c + c4 + q] = outv[q];
+                fence_async_smem();
+                eval_barrier();
+                if (threadIdx.x == 0 && !*reinterpret_cast<volatile int *>(s_err)) {
+                    asm volatile(
+                        "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
+                            p.W + r0 * p.c),
+                        "r"(smem_u32(stg)), "r"((uint32_t)(BR * p.c * 4))
+                        : "memory");
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
+            } else if (row < rows_valid) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c4 + q < p.c) atomicAdd(p.W + (r0 + row) * p.c + c4 + q, outv[q]);
+            }
+        }
+        if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == SNEVAL) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.ncols_tmem)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *s_err) atomicOr(p.err, *s_err);
+}
+
+// 128-point tiles, coordinate-major, log2 e folded in, far padding (as point_tiles_kernel)
+__global__ void sym_point_tiles_kernel(const float *Xs, int64_t n, int d, float factor, int64_t ntiles,
+                                       float *Xp) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)BR * d;
+    if (idx >= per * ntiles) return;
+    const int64_t t = idx / per;
+    const int rem = (int)(idx % per);
+    const int a = rem / BR, jj = rem % BR;
+    const int64_t i = t * BR + jj;
+    Xp[idx] = i < n ? Xs[i * d + a] * factor : 1e18f;
+}
+
+// V operand image per 128-point tile: 16 columns x 128 K values, canonical K-major
+// (byte offset (col/8)*2048 + (jj/8)*128 + (col%8)*16 + (jj%8)*2), hi then lo.
+template <bool BF16, int NPROD>
+__global__ void sym_image_kernel(const float *V, int64_t n, int c, int ntiles, const float *scale,
+                                 uint8_t *img) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t per_tile = (int64_t)SYM_N * (BR / 8);
+    if (idx >= per_tile * ntiles) return;
+    const int64_t t = idx / per_tile;
+    const int rem = (int)(idx % per_tile);
+    const int cr = rem & 7;
+    const int kq = (rem >> 3) % (BR / 8);
+    const int g = rem / (8 * (BR / 8));
+    const int col = g * 8 + cr;
+    const float s = scale[col];
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int64_t j = t * BR + kq * 8 + q;
+        v[q] = (j < n && col < c) ? V[j * c + col] * s : 0.f;
+    }
+    uint4 hi;
+    hi.x = pack2<BF16>(v[0], v[1]); hi.y = pack2<BF16>(v[2], v[3]);
+    hi.z = pack2<BF16>(v[4], v[5]); hi.w = pack2<BF16>(v[6], v[7]);
+    const size_t tile_bytes = (size_t)(NPROD == 3 ? 2 : 1) * SYM_N * BR * 2;
+    uint8_t *base = img + (size_t)t * tile_bytes;
+    const size_t off = (size_t)g * CORE_SBO + (size_t)kq * 128 + (size_t)cr * 16;
+    *reinterpret_cast<uint4 *>(base + off) = hi;
+    if (NPROD == 3) {
+        uint4 lo;
+        uint32_t *hp = &hi.x, *lp = &lo.x;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const float2 f = unpack2<BF16>(hp[w]);
+            lp[w] = pack2<BF16>(v[2 * w] - f.x, v[2 * w + 1] - f.y);
+        }
+        *reinterpret_cast<uint4 *>(base + (size_t)SYM_N * BR * 2 + off) = lo;
+    }
+}
+
+__global__ void sym_colmax_kernel(const float *V, int64_t n, int c, float *part) {
+    const int col = threadIdx.x;
+    const int nb = gridDim.x;
+    const int64_t per = (n + nb - 1) / nb;
+    const int64_t r0 = blockIdx.x * per, r1 = min(n, r0 + per);
+    float m = 0.f;
+    if (col < c)
+        for (int64_t i = r0; i < r1; ++i) m = fmaxf(m, fabsf(V[i * c + col]));
+    if (col < SYM_N) part[(size_t)blockIdx.x * SYM_N + col] = m;
+}
+
+__global__ void sym_colscale_kernel(const float *part, int nb, float *scale, float *colinv) {
+    const int col = threadIdx.x;
+    if (col >= SYM_N) return;
+    float m = 0.f;
+    for (int b = 0; b < nb; ++b) m = fmaxf(m, part[(size_t)b * SYM_N + col]);
+    int e = 0;
+    if (m > 0.f) frexpf(m, &e);
+    const float s = ldexpf(1.0f, -e);
+    scale[col] = s;
+    colinv[col] = 1.0f / s;
+}
+
+int sym_stages(int d, int nprod, int c) {
+    for (int s = 4; s >= 2; --s)
+        if (make_sym_layout(d, nprod, c, s).total <= 225 * 1024) return s;
+    return 0;
+}
+
+template <int KIND, int DC, int NPROD, bool BF16>
+int launch_sym(const SymParams &p, const SymLayout &L, cudaStream_t st) {
+    auto fn = kz_sym_kernel<KIND, DC, NPROD, BF16>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e != cudaSuccess) {
+        set_error("kz_sym: cannot reserve %d bytes of shared memory: %s", L.total, cudaGetErrorString(e));
+        return LD_ERR_CUDA;
+    }
+    const double nn = (double)p.n * (double)p.n;
+    const int slot = prof_begin_launch(st, nn, 2.0 * nn * SYM_N * NPROD);
+    fn<<<p.NB, SNTHREADS, L.total, st>>>(p, L);
+    prof_end_launch(st, slot);
+    return check_launch("kz_sym_kernel");
+}
+
+template <int KIND, int NPROD, bool BF16>
+int launch_sym_d(const SymParams &p, const SymLayout &L, cudaStream_t st) {
+    switch (p.d) {
+        case 1: return launch_sym<KIND, 1, NPROD, BF16>(p, L, st);
+        case 2: return launch_sym<KIND, 2, NPROD, BF16>(p, L, st);
+        case 3: return launch_sym<KIND, 3, NPROD, BF16>(p, L, st);
+        case 4: return launch_sym<KIND, 4, NPROD, BF16>(p, L, st);
+        default: return launch_sym<KIND, 0, NPROD, BF16>(p, L, st);
+    }
+}
+
+}  // namespace
+
+bool kz_sym_eligible(int64_t n, int d, int c, int precision) {
+    const int nprod = precision == LD_F16X3_TC ? 3 : 1;
+    return c <= SYM_N && n >= 2 * BR && d <= 8 && sym_stages(d, nprod, c) > 0;
+}
+
+size_t kz_sym_workspace(int64_t n, int d, int c, int precision) {
+    const int64_t NB = (n + BR - 1) / BR;
+    const int nprod = precision == LD_F16X3_TC ? 3 : 1;
+    Arena a;
+    a.measuring = true;
+    a.take<float>((size_t)NB * BR * d);
+    a.take<uint8_t>((size_t)NB * (nprod == 3 ? 2 : 1) * SYM_N * BR * 2);
+    a.take<float>(SYM_N);
+    a.take<float>(SYM_N);
+    a.take<float>((size_t)256 * SYM_N);
+    a.take<int>(4);
+    (void)c;
+    return a.off;
+}
+
+int kz_sym(const float *Xs, int64_t n, int d, int kind, double variance, double noise, const float *V, float *W,
+           int c, int precision, Arena &ws, cudaStream_t st) {
+    const int64_t NB = (n + BR - 1) / BR;
+    const int nprod = precision == LD_F16X3_TC ? 3 : 1;
+    const bool bf16 = precision == LD_BF16_TC;
+    const size_t mark = ws.off;
+    float *Xp = ws.take<float>((size_t)NB * BR * d);
+    uint8_t *img = ws.take<uint8_t>((size_t)NB * (nprod == 3 ? 2 : 1) * SYM_N * BR * 2);
+    float *scale = ws.take<float>(SYM_N);
+    float *colinv = ws.take<float>(SYM_N);
+    float *part = ws.take<float>((size_t)256 * SYM_N);
+    int *err = ws.take<int>(4);
+    if (ws.overflow || !Xp) {
+        set_error("kz_sym: workspace too small");
+        ws.off = mark;
+        return LD_ERR_WORKSPACE;
+    }
+    int code = [&]() -> int {
+        const float factor = kind == LD_RBF ? 1.2011224087864498f : 1.4426950408889634f;
+        const int64_t cnt = NB * BR * d;
+        sym_point_tiles_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(Xs, n, d, factor, NB, Xp);
+        sym_colmax_kernel<<<256, 32, 0, st>>>(V, n, c, part);
+        sym_colscale_kernel<<<1, 32, 0, st>>>(part, 256, scale, colinv);
+        const int64_t nthr = NB * SYM_N * (BR / 8);
+        const unsigned gb = (unsigned)((nthr + 255) / 256);
+        if (bf16) sym_image_kernel<true, 1><<<gb, 256, 0, st>>>(V, n, c, (int)NB, scale, img);
+        else if (nprod == 3) sym_image_kernel<false, 3><<<gb, 256, 0, st>>>(V, n, c, (int)NB, scale, img);
+        else sym_image_kernel<false, 1><<<gb, 256, 0, st>>>(V, n, c, (int)NB, scale, img);
+        LD_TRY(check_launch("kz_sym prep", 4));
+        LD_CHECK_CUDA(cudaMemsetAsync(W, 0, sizeof(float) * (size_t)n * c, st));
+        LD_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+        SymParams p;
+        p.Xp = Xp;
+        p.img = img;
+        p.V = V;
+        p.colinv = colinv;
+        p.W = W;
+        p.n = n;
+        p.d = d;
+        p.c = c;
+        p.NB = (int)NB;
+        const int tcols = (nprod == 3 ? 4 : 3) * SYM_N;  // D (x2 when drained) + two D'
+        p.ncols_tmem = tcols <= 32 ? 32 : (tcols <= 64 ? 64 : 128);
+        p.bulk_ok = (reinterpret_cast<uintptr_t>(W) % 16 == 0) && ((c * 4) % 16 == 0);
+        p.variance = (float)variance;
+        p.noise = (float)noise;
+        p.err = err;
+        const SymLayout L = make_sym_layout(d, nprod, c, sym_stages(d, nprod, c));
+        if (kind == LD_RBF) {
+            if (bf16) LD_TRY(launch_sym_d<LD_RBF, 1, true>(p, L, st));
+            else if (nprod == 3) LD_TRY(launch_sym_d<LD_RBF, 3, false>(p, L, st));
+            else LD_TRY(launch_sym_d<LD_RBF, 1, false>(p, L, st));
+        } else {
+            if (bf16) LD_TRY(launch_sym_d<LD_MATERN52, 1, true>(p, L, st));
+            else if (nprod == 3) LD_TRY(launch_sym_d<LD_MATERN52, 3, false>(p, L, st));
+            else LD_TRY(launch_sym_d<LD_MATERN52, 1, false>(p, L, st));
+        }
+        int herr = 0;
+        LD_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LD_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (herr) {
+            set_error("kz_sym: a device-side wait timed out (error word %d)", herr);
+            return LD_ERR_DEVICE_TIMEOUT;
+        }
+        return LD_OK;
+    }();
+    ws.off = mark;
+    return code;
+}
+
+}  // namespace ld

@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("kind", [api.RBF, api.MATERN52])
-@pytest.mark.parametrize("n,d,c", [(1000, 2, 16), (333, 3, 5), (777, 4, 33), (64, 1, 1)])
+@pytest.mark.parametrize("n,d,c", [(1000, 2, 16), (333, 3, 5), (777, 4, 33), (64, 1, 1), (300, 12, 4), (257, 20, 3)])
 def test_kz_fp64_matches_dense_oracle(kind, n, d, c):
     X = inputs.points(n, d, "uniform", seed=3)
     V = inputs.gaussian(n, c, seed=4)
@@ -99,3 +99,34 @@ def test_kz_f16x3_sampled_rows_at_large_n():
     rows = np.concatenate([np.random.default_rng(1).choice(n, 24, replace=False), [0, n - 1]])
     ref = kernels.kz_rows(X, V, rows, api.MATERN52, 0.1, 1.0, 1e-2)
     assert relerr(W[rows], ref) < 2 * np.sqrt(n) * 2.0 ** -24 + 2.0 ** -19
+
+
+def test_kz_bench_workload_sampled_rows():
+    # the product exactly as the timed estimate calls it: n = 2^20 Matern-5/2 points
+    # in [0,1]^4, lengthscale 0.1, 16 columns (symmetric kernel), hi/lo fp16
+    from paper_2405_03474_gb300.inputs import WORKLOADS
+    w = WORKLOADS["matern_n1048576_d4"]
+    n, d, c = w["n"], w["d"], w["probes"]
+    X = inputs.points(n, d, w["dist"], seed=inputs.SEED_POINTS)
+    V = inputs.gaussian(n, c, seed=7)
+    k = api.Kernel(w["kind"], w["lengthscale"], w["variance"], w["noise"])
+    W = host(api.ld_kz(cuda(X), cuda(V, torch.float32), k, "f16x3_tc"))
+    rows = np.concatenate([np.random.default_rng(3).choice(n, 30, replace=False), [0, 127, 128, n - 1]])
+    ref = kernels.kz_rows(X, V, rows, w["kind"], w["lengthscale"], w["variance"], w["noise"])
+    assert relerr(W[rows], ref) < 2 * np.sqrt(n) * 2.0 ** -24 + 2.0 ** -19
+
+
+# The symmetric product (c <= 16): one CTA per 128-row block visits half of the
+# blocks, so cover NB = 2 (even, tie rule), odd NB, a ragged last block, 1..16
+# columns, c * 4 not a multiple of 16 (per-element adds instead of bulk adds)
+# and a dimension above 4 (the generic-d instance).
+@pytest.mark.parametrize("prec", ["f16x3_tc", "f16_tc", "bf16_tc"])
+@pytest.mark.parametrize("kind", [api.RBF, api.MATERN52])
+@pytest.mark.parametrize("n,d,c", [(256, 2, 16), (257, 3, 7), (384, 4, 1), (4133, 4, 16), (1536, 1, 12), (700, 6, 9)])
+def test_kz_symmetric_tensor_core_matches_oracle(prec, kind, n, d, c):
+    X = inputs.points(n, d, "uniform", seed=31)
+    V = inputs.gaussian(n, c, seed=32)
+    k = api.Kernel(kind, 0.2, 0.9, 3e-2)
+    W = host(api.ld_kz(cuda(X), cuda(V, torch.float32), k, prec))
+    ref = kernels.kernel_matrix(X, kind, 0.2, 0.9, 3e-2) @ V
+    assert relerr(W, ref) < TC_TOL[prec]

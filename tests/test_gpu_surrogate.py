@@ -101,4 +101,6 @@ def test_surrogate_gain_over_the_estimator():
     # outside the box the estimator answers
     far = np.array([[3.0, 1.0, 0.05]])
     p, out = hs.predict(far)
-    assert out[0] and p[0] == pytest.approx(est(far[0]), rel=1e-12)
+    # (the symmetric kernel product adds the blocks of different CTAs in arrival order,
+    # so two estimates of one theta agree to fp32 rounding of the sums, not bit for bit)
+    assert out[0] and p[0] == pytest.approx(est(far[0]), rel=1e-6)
