@@ -95,6 +95,14 @@ typedef struct {
                                 workspace) and apply it from HBM; 0: matrix-free */
     uint64_t seed;           /* SplitMix64 seed of the probes when probes_dev is NULL */
     double rel_tol;          /* stop when max_i ||r_i|| / ||z_i|| < rel_tol (seed system) */
+    int32_t probe_kind;      /* 0: Rademacher (Section 3); 1: N(0, 1) by Box-Muller from the
+                                same SplitMix64 stream (counters 2k, 2k+1; device-drawn only);
+                                2: normal orthogonal (Appendix, probe types): per block of
+                                probes_per_block (<= n) columns, the orthonormal factor (R
+                                diagonal > 0) of the Gaussian block of those columns, each
+                                column scaled by the norm of Gaussian column 2^30 + its
+                                index (a chi_n draw); device-drawn only */
+    int32_t reserved;
 } ld_options;
 
 typedef struct {
@@ -107,6 +115,9 @@ typedef struct {
     double max_resid[5];  /* residual check: max_i ||z_i - (B + sigma_j) x_ij|| / ||z_i||,
                              fp64 norms; entries beyond the order are 0 */
     double final_rel_resid; /* max_i ||r_i|| / ||z_i|| of the seed system at exit */
+    double slq_logdet;    /* stochastic Lanczos quadrature (Ubaru et al., Section 3's
+                             comparison method) from the same Lanczos tridiagonals:
+                             log det P + (1/s) sum_i |z_i|^2 sum_k q_ik^2 log theta_ik */
 } ld_result;
 
 typedef struct ld_precond ld_precond;
@@ -166,6 +177,11 @@ int ld_dense_materialize(const double *X_dev, int64_t n, int32_t d, ld_kernel ke
 int ld_dense_kz(const void *M_dev, int64_t n, const void *V_dev, void *W_dev, int32_t c,
                 int32_t precision, void *stream);
 
+/* N(0, 1) block (float64, row-major n-by-s): entry (i, j) is
+ * sqrt(-2 ln u1) cos(2 pi u2) (Box & Muller 1958) with u1, u2 the (0, 1) uniforms
+ * (top 53 bits + 1/2) * 2^-53 of SplitMix64 outputs 2k and 2k + 1, k = (col0 + j) n + i. */
+int ld_gaussian(uint64_t seed, int64_t n, int32_t s, int32_t col0, double *Z_dev, void *stream);
+
 /* Rademacher block from the SplitMix64 stream (Steele, Lea & Flood 2014):
  * Z[i, j] (row-major n-by-s int8) uses counter (col0 + j) * n + i and is +1
  * when bit 63 of the output is 0, else -1 (Algorithm 1 step 1 with D the
@@ -185,12 +201,20 @@ int ld_rademacher(uint64_t seed, int64_t n, int32_t s, int32_t col0,
  * precision: LD_FP64 keeps factors in float64 (products FP64); any other
  * value keeps n-by-rank factors in float32, r-by-r factors in float64, and
  * runs the M products in that precision.
- * rank = 0 gives P = I (Appendix "Identity"). */
+ * rank = 0 gives P = diag(M) (Appendix "Diagonal"); P = NULL in
+ * logdet_estimate means P = I (Appendix "Identity"). */
 size_t precond_workspace_size(int64_t n, int32_t d, int32_t rank, int32_t precision);
 int precond_build(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
                   int32_t rank, int32_t power_iters, uint64_t seed,
                   int32_t precision, void *ws, size_t ws_bytes, void *stream,
                   ld_precond **out);
+/* Appendix "Truncated Randomized SVD plus scaling": the same A, with the
+ * diagonal replaced by the constant a > 0 (the paper takes a = jitter + noise
+ * variance): P = a I + A A^T.  Same workspace as precond_build. */
+int precond_build_scaled(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
+                         int32_t rank, int32_t power_iters, uint64_t seed, double a,
+                         int32_t precision, void *ws, size_t ws_bytes, void *stream,
+                         ld_precond **out);
 /* Build the same handle from host A (n-by-rank row-major) and D (n). */
 int precond_import(const double *A_host, const double *D_host, int64_t n,
                    int32_t rank, int32_t precision, void *stream,

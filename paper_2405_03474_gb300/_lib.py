@@ -50,13 +50,13 @@ class LdOptions(ctypes.Structure):
     _fields_ = [("order", c_int32), ("num_probes", c_int32), ("probes_per_block", c_int32),
                 ("max_iters", c_int32), ("fixed_iters", c_int32), ("precision", c_int32),
                 ("residual_check", c_int32), ("dense", c_int32), ("seed", c_uint64),
-                ("rel_tol", c_double)]
+                ("rel_tol", c_double), ("probe_kind", c_int32), ("reserved", c_int32)]
 
 
 class LdResult(ctypes.Structure):
     _fields_ = [("logdet", c_double), ("logdet_P", c_double), ("trace_est", c_double),
                 ("std_err", c_double), ("iters", c_int32), ("converged", c_int32),
-                ("max_resid", c_double * 5), ("final_rel_resid", c_double)]
+                ("max_resid", c_double * 5), ("final_rel_resid", c_double), ("slq_logdet", c_double)]
 
 
 _P = c_void_p
@@ -74,9 +74,12 @@ _SIGS = {
     "ld_dense_materialize": (c_int32, [_P, c_int64, c_int32, LdKernel, c_int32, _P, _P]),
     "ld_dense_kz": (c_int32, [_P, c_int64, _P, _P, c_int32, c_int32, _P]),
     "ld_rademacher": (c_int32, [c_uint64, c_int64, c_int32, c_int32, _P, _P]),
+    "ld_gaussian": (c_int32, [c_uint64, c_int64, c_int32, c_int32, _P, _P]),
     "precond_workspace_size": (c_size_t, [c_int64, c_int32, c_int32, c_int32]),
     "precond_build": (c_int32, [_P, c_int64, c_int32, LdKernel, c_int32, c_int32, c_uint64, c_int32,
                                 _P, c_size_t, _P, _P]),
+    "precond_build_scaled": (c_int32, [_P, c_int64, c_int32, LdKernel, c_int32, c_int32, c_uint64, c_double,
+                                       c_int32, _P, c_size_t, _P, _P]),
     "precond_import": (c_int32, [_P, _P, c_int64, c_int32, c_int32, _P, _P]),
     "precond_export": (c_int32, [_P, _P, _P, _P, _P]),
     "precond_info": (c_int32, [_P, _P, _P, _P, _P]),

@@ -128,6 +128,14 @@ def ld_dense_kz(M, V, precision="fp32", stream=None):
     return W
 
 
+def ld_gaussian(seed, n, s, col0=0, device="cuda", stream=None):
+    """n-by-s float64 N(0,1) block (Box-Muller over SplitMix64(seed))."""
+    lib = _lib.load()
+    Z = torch.empty((n, s), dtype=torch.float64, device=device)
+    check(lib.ld_gaussian(seed, n, s, col0, _ptr(Z), _stream(stream)), "ld_gaussian")
+    return Z
+
+
 def ld_rademacher(seed, n, s, col0=0, device="cuda", stream=None):
     """n-by-s int8 Rademacher block from SplitMix64(seed)."""
     lib = _lib.load()
@@ -161,6 +169,19 @@ class Precond:
         h = ctypes.c_void_p()
         check(lib.precond_build(_ptr(X), n, d, kernel.c(), rank, power_iters, seed, p, _ptr(ws), nb,
                                 _stream(stream), ctypes.byref(h)), "precond_build")
+        return cls(h, p)
+
+    @classmethod
+    def build_scaled(cls, X, kernel, rank, a, power_iters=2, seed=2, precision="fp32", stream=None):
+        """P = a I + A A^T (Appendix "plus scaling")."""
+        lib = _lib.load()
+        X = _points(X)
+        p = _prec(precision)
+        n, d = X.shape
+        ws, nb = _workspace(lib.precond_workspace_size(n, d, rank, p), X.device)
+        h = ctypes.c_void_p()
+        check(lib.precond_build_scaled(_ptr(X), n, d, kernel.c(), rank, power_iters, seed, float(a), p, _ptr(ws),
+                                       nb, _stream(stream), ctypes.byref(h)), "precond_build_scaled")
         return cls(h, p)
 
     @classmethod
@@ -210,10 +231,11 @@ class Precond:
 
 
 def make_options(order=3, num_probes=16, probes_per_block=None, max_iters=1000, fixed_iters=0,
-                 precision="fp32", residual_check=False, seed=1, rel_tol=1e-6, dense=False):
+                 precision="fp32", residual_check=False, seed=1, rel_tol=1e-6, dense=False, probe_kind="rademacher"):
+    kind = {"rademacher": 0, "gaussian": 1, "orthogonal": 2}[probe_kind] if isinstance(probe_kind, str) else int(probe_kind)
     return LdOptions(int(order), int(num_probes), int(probes_per_block or num_probes), int(max_iters),
                      int(fixed_iters), _prec(precision), int(bool(residual_check)), int(bool(dense)), int(seed),
-                     float(rel_tol))
+                     float(rel_tol), kind, 0)
 
 
 def _result_dict(res, status, per_probe=None):
@@ -221,6 +243,7 @@ def _result_dict(res, status, per_probe=None):
         "logdet": res.logdet, "logdet_P": res.logdet_P, "trace_est": res.trace_est,
         "std_err": res.std_err, "iters": res.iters, "converged": bool(res.converged),
         "max_resid": list(res.max_resid), "final_rel_resid": res.final_rel_resid, "status": status,
+        "slq_logdet": res.slq_logdet,
     }
     if per_probe is not None:
         out["per_probe"] = per_probe

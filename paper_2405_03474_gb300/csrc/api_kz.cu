@@ -8,7 +8,9 @@ int check_kz_args(const double *X, int64_t n, int d, const ld_kernel &k, const v
                   int c, int precision) {
     LD_REQUIRE(X && V && W && n > 0 && c > 0, "ld_kz: bad pointers or sizes");
     LD_REQUIRE(V != W, "ld_kz: W must not alias V");
-    LD_REQUIRE(d >= 1 && d <= 8, "ld_kz: d must be in [1, 8]");
+    LD_REQUIRE(d >= 1 && d <= 32, "ld_kz: d must be in [1, 32]");
+    LD_REQUIRE(d <= 8 || precision == LD_FP64 || precision == LD_FP32,
+               "ld_kz: tensor-core precisions support d <= 8");
     LD_REQUIRE(c <= 4096, "ld_kz: at most 4096 columns");
     LD_REQUIRE(k.lengthscale > 0 && k.variance > 0 && k.noise >= 0 &&
                    (k.kind == LD_RBF || k.kind == LD_MATERN52),

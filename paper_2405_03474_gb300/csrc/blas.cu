@@ -226,6 +226,19 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
     return z ^ (z >> 31);
 }
 
+// N(0,1) by Box-Muller from SplitMix64 outputs 2k, 2k+1 (uniforms (m + 1/2) 2^-53)
+template <typename T>
+__global__ void gaussian_kernel(uint64_t seed, int64_t n, int s, int col0, T *Z) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * s) return;
+    int64_t i = t / s;
+    int j = (int)(t % s);
+    uint64_t k = (uint64_t)(col0 + j) * (uint64_t)n + (uint64_t)i;
+    const double u1 = ((double)(splitmix64_at(seed, 2 * k) >> 11) + 0.5) * 1.1102230246251565e-16;
+    const double u2 = ((double)(splitmix64_at(seed, 2 * k + 1) >> 11) + 0.5) * 1.1102230246251565e-16;
+    Z[t] = (T)(sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+}
+
 __global__ void rademacher_kernel(uint64_t seed, int64_t n, int s, int col0, int8_t *Z) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n * s) return;
@@ -314,6 +327,15 @@ int axpy(int64_t count, T alpha, const T *x, T *y, cudaStream_t st) {
     return check_launch("axpy");
 }
 
+template <typename T>
+int gaussian(uint64_t seed, int64_t n, int s, int col0, T *Z, cudaStream_t st) {
+    if (n * s == 0) return LD_OK;
+    gaussian_kernel<T><<<blocks_for(n * s), 256, 0, st>>>(seed, n, s, col0, Z);
+    return check_launch("gaussian");
+}
+template int gaussian<float>(uint64_t, int64_t, int, int, float *, cudaStream_t);
+template int gaussian<double>(uint64_t, int64_t, int, int, double *, cudaStream_t);
+
 int rademacher(uint64_t seed, int64_t n, int s, int col0, int8_t *Z, cudaStream_t st) {
     if (n * s == 0) return LD_OK;
     rademacher_kernel<<<blocks_for(n * s), 256, 0, st>>>(seed, n, s, col0, Z);
@@ -347,4 +369,13 @@ extern "C" int ld_rademacher(uint64_t seed, int64_t n, int32_t s, int32_t col0, 
         return LD_ERR_INVALID;
     }
     return ld::rademacher(seed, n, s, col0, Z_dev, (cudaStream_t)stream);
+}
+
+extern "C" int ld_gaussian(uint64_t seed, int64_t n, int32_t s, int32_t col0, double *Z_dev, void *stream) {
+    ld::clear_error();
+    if (n < 0 || s < 0 || col0 < 0 || (n * s > 0 && !Z_dev)) {
+        ld::set_error("ld_gaussian: bad arguments");
+        return LD_ERR_INVALID;
+    }
+    return ld::gaussian<double>(seed, n, s, col0, Z_dev, (cudaStream_t)stream);
 }

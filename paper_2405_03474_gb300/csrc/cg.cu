@@ -209,6 +209,82 @@ __global__ void quadrature_kernel(const ColState *cs, const double *hist_a, cons
     bracket[c] = acc;
 }
 
+// Eigenvalues of a symmetric tridiagonal matrix (diag a[0..m), off-diagonal
+// b[0..m-1)) and the first components q of its eigenvectors, by implicit
+// symmetric QR steps with the Wilkinson shift (Golub & Van Loan, "Matrix
+// Computations", symmetric QR algorithm): each step chases a bulge with Givens
+// rotations G = [c -s; s c]; only the first row of the accumulated rotations is
+// kept, which is what Gauss quadrature needs (Golub & Welsch).  Arrays are
+// overwritten (a -> eigenvalues).  Returns false if it did not converge.
+__device__ bool tridiag_eig_first_row(double *a, double *b, double *q, int m) {
+    for (int i = 0; i < m; ++i) q[i] = i == 0 ? 1.0 : 0.0;
+    int h = m - 1, guard = 0;
+    while (h > 0) {
+        if (++guard > 60 * m) return false;
+        if (fabs(b[h - 1]) <= 1e-15 * (fabs(a[h - 1]) + fabs(a[h]))) {
+            b[h - 1] = 0.0;
+            --h;
+            continue;
+        }
+        int l = h - 1;
+        while (l > 0 && fabs(b[l - 1]) > 1e-15 * (fabs(a[l - 1]) + fabs(a[l]))) --l;
+        // Wilkinson shift: eigenvalue of the trailing 2x2 block closer to a[h]
+        const double dd = 0.5 * (a[h - 1] - a[h]);
+        const double bb = b[h - 1];
+        const double mu = a[h] - bb * bb / (dd + copysign(hypot(dd, bb), dd));
+        double x = a[l] - mu, y = b[l];
+        for (int k = l; k < h; ++k) {
+            const double r = hypot(x, y);
+            const double c = r > 0.0 ? x / r : 1.0, sn = r > 0.0 ? y / r : 0.0;
+            if (k > l) b[k - 1] = r;  // the bulge is absorbed
+            const double ap = a[k], aq = a[k + 1], bp = b[k];
+            a[k] = c * c * ap + 2.0 * c * sn * bp + sn * sn * aq;
+            a[k + 1] = sn * sn * ap - 2.0 * c * sn * bp + c * c * aq;
+            b[k] = c * sn * (aq - ap) + (c * c - sn * sn) * bp;
+            const double qp = q[k], qq = q[k + 1];
+            q[k] = c * qp + sn * qq;
+            q[k + 1] = -sn * qp + c * qq;
+            if (k + 1 < h) {  // new bulge at (k, k + 2)
+                y = sn * b[k + 1];
+                b[k + 1] *= c;
+                x = b[k];
+            }
+        }
+    }
+    return true;
+}
+
+// Stochastic Lanczos quadrature (Ubaru, Chen & Saad 2017; the comparison method of
+// Section 3) from the same CG coefficients: T_B = T_seed - sigma_min I,
+// z^T log(B) z ~ |z|^2 sum_k q_k^2 log(theta_k).  scratch: 3 * max_iters per column.
+__global__ void slq_kernel(const ColState *cs, const double *hist_a, const double *hist_b, int s,
+                           double sigma_min, int max_iters, double *scratch, double *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= s) return;
+    const ColState &st = cs[c];
+    const int t = st.t;
+    double *a = scratch + (size_t)c * 3 * max_iters;
+    double *b = a + max_iters;
+    double *q = b + max_iters;
+    if (t == 0) {
+        out[c] = 0.0;
+        return;
+    }
+    for (int k = 0; k < t; ++k) {
+        const double ak = hist_a[(size_t)k * s + c];
+        a[k] = 1.0 / ak + (k > 0 ? hist_b[(size_t)(k - 1) * s + c] / hist_a[(size_t)(k - 1) * s + c] : 0.0) -
+               sigma_min;
+        if (k + 1 < t) b[k] = sqrt(hist_b[(size_t)k * s + c]) / ak;
+    }
+    if (!tridiag_eig_first_row(a, b, q, t)) {
+        out[c] = nan("");
+        return;
+    }
+    double acc = 0.0;
+    for (int k = 0; k < t; ++k) acc += q[k] * q[k] * log(fmax(a[k], 1e-300));
+    out[c] = st.znorm2 * acc;
+}
+
 // gather probe block columns [col0, col0+s) of an n x S int8 matrix into T
 template <typename T>
 __global__ void gather_probes_kernel(const int8_t *P, int64_t n, int S, int col0, int s, T *Z) {
@@ -248,7 +324,7 @@ template <typename T>
 struct Bufs {
     T *Xs, *Z, *r, *p, *Bp, *y, *w, *xs, *ps;
     int8_t *Zi8;
-    double *dots, *part, *hist_a, *hist_b, *q, *bracket;
+    double *dots, *part, *hist_a, *hist_b, *q, *bracket, *slq_scratch, *slq;
     ColState *cs;
     int *n_active;
     // precond apply scratch
@@ -284,6 +360,8 @@ void carve(Arena &a, Bufs<T> &b, int64_t n, int d, const ld_precond *P, int s, i
     b.hist_b = a.take<double>((size_t)max_iters * s + 1);
     b.q = a.take<double>((size_t)s * 5);
     b.bracket = a.take<double>((size_t)s);
+    b.slq_scratch = a.take<double>((size_t)s * 3 * max_iters + 1);
+    b.slq = a.take<double>((size_t)s);
     b.cs = a.take<ColState>((size_t)s);
     b.n_active = a.take<int>(4);
     const int r = P ? P->r : 0;
@@ -315,7 +393,11 @@ size_t run_bytes(int64_t n, int d, const ld_precond *P, int s, int m, int max_it
     meas.measuring = true;
     Bufs<T> b;
     carve<T>(meas, b, n, d, P, s, m, max_iters, precision, vectors, extra, dense);
-    if (!dense) meas.take<char>(kz_any_workspace<T>(n, d, extra ? std::max(s, s * m) : s, precision));
+    // the free tail serves the kernel product and, before the CG starts, the
+    // orthogonal-probe cores
+    size_t tail = orth_probe_tail_bytes(n, s);
+    if (!dense) tail = std::max(tail, kz_any_workspace<T>(n, d, extra ? std::max(s, s * m) : s, precision));
+    meas.take<char>(tail);
     return meas.off;
 }
 
@@ -340,7 +422,7 @@ int apply_B(const ld_precond *P, Bufs<T> &b, const T *Xs, int64_t n, int d, cons
 }
 
 struct RunOut {
-    std::vector<double> brackets;
+    std::vector<double> brackets, slq;
     int iters = 0;
     bool converged = true;
     double final_rel = 0.0;
@@ -378,11 +460,16 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
         for (int j = 0; j < 5; ++j) sh.delta[j] = j < m ? rk.sigma[j] - smin : 0.0;
         const double tol2 = o.rel_tol * o.rel_tol;
         out.brackets.assign(o.num_probes, 0.0);
+        out.slq.assign(o.num_probes, 0.0);
         for (int blk = 0; blk < nblocks; ++blk) {
             // probes (Algorithm 1 step 1)
             if (probes) {
                 gather_probes_kernel<T><<<nb(ns), 256, 0, st>>>(probes, n, o.num_probes, blk * s, s, b.Z);
                 LD_TRY(check_launch("gather_probes"));
+            } else if (o.probe_kind == 1) {
+                LD_TRY(gaussian<T>(o.seed, n, s, blk * s, b.Z, st));
+            } else if (o.probe_kind == 2) {
+                LD_TRY(orthogonal_probes<T>(o.seed, n, s, blk * s, b.Z, b.Bp, b.y, b.w, a, st));
             } else {
                 LD_TRY(rademacher(o.seed, n, s, blk * s, b.Zi8, st));
                 LD_TRY(int8_to<T>(b.Zi8, b.Z, (int64_t)ns, st));
@@ -424,9 +511,13 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
             quadrature_kernel<<<nb(s, 128), 128, 0, st>>>(b.cs, b.hist_a, b.hist_b, s, rk, smin, b.q,
                                                          b.bracket);
             LD_TRY(check_launch("quadrature"));
+            slq_kernel<<<nb(s, 64), 64, 0, st>>>(b.cs, b.hist_a, b.hist_b, s, smin, max_iters, b.slq_scratch, b.slq);
+            LD_TRY(check_launch("slq"));
             std::vector<ColState> cs(s);
             LD_CHECK_CUDA(cudaMemcpyAsync(out.brackets.data() + (size_t)blk * s, b.bracket,
                                           sizeof(double) * s, cudaMemcpyDeviceToHost, st));
+            LD_CHECK_CUDA(cudaMemcpyAsync(out.slq.data() + (size_t)blk * s, b.slq, sizeof(double) * s,
+                                          cudaMemcpyDeviceToHost, st));
             LD_CHECK_CUDA(cudaMemcpyAsync(cs.data(), b.cs, sizeof(ColState) * s, cudaMemcpyDeviceToHost, st));
             LD_CHECK_CUDA(cudaStreamSynchronize(st));
             for (int c = 0; c < s; ++c) {
@@ -487,7 +578,9 @@ int validate(const double *X, int64_t n, int d, const ld_kernel &k, const ld_pre
              const ld_options *o, bool grad) {
     LD_REQUIRE(o != nullptr, "options are NULL");
     LD_REQUIRE(X != nullptr && n > 0, "need n > 0 points");
-    LD_REQUIRE(d >= 1 && d <= 8, "d must be in [1, 8]");
+    LD_REQUIRE(d >= 1 && d <= 32, "d must be in [1, 32]");
+    LD_REQUIRE(d <= 8 || o->precision == LD_FP64 || o->precision == LD_FP32 || o->dense,
+               "tensor-core precisions support d <= 8");
     LD_REQUIRE(k.lengthscale > 0 && k.variance > 0 && k.noise >= 0 &&
                    (k.kind == LD_RBF || k.kind == LD_MATERN52),
                "bad kernel parameters");
@@ -501,6 +594,10 @@ int validate(const double *X, int64_t n, int d, const ld_kernel &k, const ld_pre
     LD_REQUIRE(o->fixed_iters > 0 || o->rel_tol > 0, "rel_tol must be > 0 without fixed_iters");
     LD_REQUIRE(o->precision >= LD_FP64 && o->precision <= LD_F16X3_TC, "bad precision");
     LD_REQUIRE(o->dense == 0 || o->dense == 1, "dense must be 0 or 1");
+    LD_REQUIRE(o->probe_kind >= 0 && o->probe_kind <= 2,
+               "probe_kind must be 0 (Rademacher), 1 (Gaussian) or 2 (normal orthogonal)");
+    LD_REQUIRE(o->probe_kind != 2 || (o->probes_per_block <= n && o->num_probes < ORF_NORM_COL0),
+               "orthogonal probes need probes_per_block <= n");
     LD_REQUIRE(o->dense == 0 || n <= (int64_t)1 << 18, "dense mode keeps n*n words: n <= 262144");
     if (P) {
         LD_REQUIRE(P->n == n, "preconditioner built for n = %lld, not %lld", (long long)P->n, (long long)n);
@@ -530,6 +627,9 @@ void fill_result(const RunOut &r, const ld_precond *P, const ld_options &o, ld_r
     out->converged = r.converged ? 1 : 0;
     for (int j = 0; j < 5; ++j) out->max_resid[j] = r.max_resid[j];
     out->final_rel_resid = r.final_rel;
+    double slq = 0.0;
+    for (double v : r.slq) slq += v;
+    out->slq_logdet = ldP + slq / S;
     if (per_probe)
         for (int i = 0; i < S; ++i) per_probe[i] = r.brackets[i];
     (void)o;
@@ -562,6 +662,8 @@ int logdet_estimate(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, c
     clear_error();
     LD_REQUIRE(out != nullptr, "logdet_estimate: out is NULL");
     LD_TRY(validate(X_dev, n, d, kern, P, opt, false));
+    LD_REQUIRE(!(probes_dev && opt->probe_kind != 0),
+               "Gaussian and orthogonal probes are drawn on the device (probes_dev = NULL)");
     RunOut r;
     cudaStream_t st = (cudaStream_t)stream;
     int code = opt->precision == LD_FP64

@@ -125,6 +125,11 @@ int dense_product(const T *M, int64_t n, const T *V, T *W, int c, cudaStream_t s
 
 // tensor-core product (float vectors)
 size_t kz_tc_workspace(int64_t n, int d, int c, int precision);
+// symmetric tensor-core product for c <= 16 (each kernel value evaluated once)
+bool kz_sym_eligible(int64_t n, int d, int c, int precision);
+size_t kz_sym_workspace(int64_t n, int d, int c, int precision);
+int kz_sym(const float *Xs, int64_t n, int d, int kind, double variance, double noise, const float *V, float *W,
+           int c, int precision, Arena &ws, cudaStream_t st);
 int kz_tc(const float *Xs, int64_t n, int d, int kind, double variance, double noise,
           const float *V, float *W, int c, int precision, Arena &ws, cudaStream_t st);
 
@@ -161,6 +166,17 @@ int scale_rows(const T *in, const T *rowscale, T *out, int64_t n, int c, cudaStr
 template <typename T>
 int axpy(int64_t count, T alpha, const T *x, T *y, cudaStream_t st);  // y += alpha x
 int rademacher(uint64_t seed, int64_t n, int s, int col0, int8_t *Z, cudaStream_t st);
+template <typename T>
+int gaussian(uint64_t seed, int64_t n, int s, int col0, T *Z, cudaStream_t st);
+// Normal orthogonal probes: Z (n x s) = Q S, Q the orthonormal factor (positive
+// R diagonal) of the Gaussian block of columns col0.., S_cc the norm of the
+// Gaussian column ORF_NORM_COL0 + col0 + c.  G, H, tmp: n x s scratch; the r x r
+// cores come from the arena's free tail (orth_probe_tail_bytes).
+constexpr int ORF_NORM_COL0 = 1 << 30;
+size_t orth_probe_tail_bytes(int64_t n, int s);
+template <typename T>
+int orthogonal_probes(uint64_t seed, int64_t n, int s, int col0, T *Z, T *G, T *H, T *tmp, Arena &a,
+                      cudaStream_t st);
 
 // ------------------------------------------------ small dense (fp64, r x r)
 // In-place lower Cholesky of A (r x r row-major, lower part used) after adding

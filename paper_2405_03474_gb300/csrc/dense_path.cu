@@ -15,20 +15,21 @@ constexpr int TI = 32, TJD = 32, RPT = 4;  // 32 x 32 tile, 4 rows per thread (b
 template <typename T, int KIND, int DC>
 __global__ void materialize_kernel(const T *__restrict__ Xs, int64_t n, int d, int64_t ntj, T var, T noise,
                                    T *__restrict__ M) {
+    constexpr int DMAX = DC > 0 ? DC : 32;
     const int dd = DC > 0 ? DC : d;
     const int64_t tile = blockIdx.x;
     const int64_t i0 = (tile / ntj) * TI, j0 = (tile % ntj) * TJD;
     const int64_t j = j0 + threadIdx.x;
-    T xj[8];
+    T xj[DMAX];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) xj[a] = (a < dd && j < n) ? Xs[j * dd + a] : T(0);
+    for (int a = 0; a < DMAX; ++a) xj[a] = (a < dd && j < n) ? Xs[j * dd + a] : T(0);
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
         const int64_t i = i0 + threadIdx.y + 8 * r;
         if (i >= n || j >= n) continue;
         T u2 = T(0);
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
+        for (int a = 0; a < DMAX; ++a) {
             if (a < dd) {
                 const T df = Xs[i * dd + a] - xj[a];
                 u2 += df * df;
@@ -91,7 +92,7 @@ int ld_dense_materialize(const double *X_dev, int64_t n, int32_t d, ld_kernel ke
                          void *M_dev, void *stream) {
     clear_error();
     LD_REQUIRE(X_dev && M_dev && n > 0 && n <= (int64_t)1 << 31, "ld_dense_materialize: bad arguments");
-    LD_REQUIRE(d >= 1 && d <= 8, "ld_dense_materialize: d must be in [1, 8]");
+    LD_REQUIRE(d >= 1 && d <= 32, "ld_dense_materialize: d must be in [1, 32]");
     LD_REQUIRE(kern.lengthscale > 0 && kern.variance > 0 && kern.noise >= 0 &&
                    (kern.kind == LD_RBF || kern.kind == LD_MATERN52),
                "ld_dense_materialize: bad kernel parameters");

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(TPB) kz_simt_kernel(const T *__restrict__ Xs, 
                                                       const T *__restrict__ V, T *__restrict__ W,
                                                       T *__restrict__ Wdl, int c, T var, T noise,
                                                       T inv_l) {
-    constexpr int DMAX = 8;
+    constexpr int DMAX = DC > 0 ? DC : 32;
     __shared__ T sx[TJ * DMAX];
     __shared__ T sv[TJ * CC];
     const int dd = DC > 0 ? DC : d;

@@ -21,8 +21,10 @@ namespace ld {
 
 namespace {
 
+// D_i = max(diag(M) - rowsumsq(A), floor), or the constant const_d when it is > 0
+// (the "plus scaling" variant P = a I + A A^T).
 template <typename T>
-__global__ void diag_resid_kernel(const T *A, int64_t n, int r, double diagM, double floor,
+__global__ void diag_resid_kernel(const T *A, int64_t n, int r, double diagM, double floor, double const_d,
                                   double *D, T *dinv, double *part) {
     __shared__ double red[32];
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -33,7 +35,7 @@ __global__ void diag_resid_kernel(const T *A, int64_t n, int r, double diagM, do
             double a = (double)A[i * r + k];
             s += a * a;
         }
-        double d = fmax(diagM - s, floor);
+        double d = const_d > 0.0 ? const_d : fmax(diagM - s, floor);
         D[i] = d;
         dinv[i] = (T)(1.0 / sqrt(d));
         lg = log(d);
@@ -259,7 +261,7 @@ void free_handle(ld_precond *P) {
 
 template <typename T>
 int build_impl(const double *X, int64_t n, int d, const ld_kernel &kern, int r, int q,
-               uint64_t seed, int precision, void *ws, size_t ws_bytes, cudaStream_t st,
+               uint64_t seed, int precision, double const_d, void *ws, size_t ws_bytes, cudaStream_t st,
                ld_precond **out) {
     Arena a;
     size_t need = build_bytes<T>(n, d, r, precision);
@@ -324,7 +326,7 @@ int build_impl(const double *X, int64_t n, int d, const ld_kernel &kern, int r, 
             }
             // D = diag(M) - rowsumsq(A), clamped; sum log D
             unsigned nb = nblk(n);
-            diag_resid_kernel<T><<<nb, 256, 0, st>>>(A, n, r, diagM, floor, P->D,
+            diag_resid_kernel<T><<<nb, 256, 0, st>>>(A, n, r, diagM, floor, const_d, P->D,
                                                     static_cast<T *>(P->dinv_sqrt), s.part);
             double *logD = s.scal + 0;
             sum_serial_kernel<<<1, 1, 0, st>>>(s.part, (int)nb, logD, 0.0, nullptr);
@@ -402,7 +404,72 @@ int import_impl(const double *A_host, const double *D_host, int64_t n, int r, in
     return LD_OK;
 }
 
+template <typename T>
+__global__ void scale_cols_sqrt_kernel(T *Z, int64_t n, int s, const double *norm2) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * s) return;
+    Z[t] = (T)((double)Z[t] * sqrt(norm2[t % s]));
+}
+
 }  // namespace
+
+// Normal orthogonal probes (the Appendix's "normal orthogonal" probe type, an
+// application of Orthogonal Monte Carlo, Yu et al. 2016): W = S Q with Q a random
+// matrix with orthonormal columns and S diagonal with chi_n entries.  Q is the
+// orthonormal factor of an n x s block of N(0, 1) draws with R's diagonal
+// positive (so its columns are Haar distributed), computed by CholeskyQR2; each
+// S entry is the norm of an independent n-vector of N(0, 1) draws, which is chi_n
+// distributed by definition.  Every column is then marginally N(0, I_n) and the
+// s columns are mutually orthogonal.
+size_t orth_probe_tail_bytes(int64_t n, int s) {
+    Arena a;
+    a.measuring = true;
+    a.take<double>((size_t)s * s);      // Tr (as double, the larger type)
+    a.take<double>((size_t)s + 64);     // squared norms
+    Small sm;
+    alloc_small<double>(a, sm, n, s, s);
+    a.take<double>(coldot_partials(n, s) + 64);
+    return a.off;
+}
+
+template <typename T>
+int orthogonal_probes(uint64_t seed, int64_t n, int s, int col0, T *Z, T *G, T *H, T *tmp, Arena &a,
+                      cudaStream_t st) {
+    const size_t mark = a.off;
+    T *Tr = a.take<T>((size_t)s * s);
+    double *norm2 = a.take<double>((size_t)s + 64);
+    Small sm;
+    alloc_small<T>(a, sm, n, s, s);
+    double *cpart = a.take<double>(coldot_partials(n, s) + 64);
+    if (a.overflow || !cpart) {
+        a.off = mark;
+        set_error("orthogonal probes: workspace too small");
+        return LD_ERR_WORKSPACE;
+    }
+    int code = [&]() -> int {
+        LD_CHECK_CUDA(cudaMemsetAsync(sm.status, 0, 16 * sizeof(int), st));
+        LD_TRY(gaussian<T>(seed, n, s, ORF_NORM_COL0 + col0, H, st));
+        LD_TRY(coldot<T>(n, s, H, H, norm2, cpart, st));
+        LD_TRY(gaussian<T>(seed, n, s, col0, G, st));
+        LD_TRY(cholqr2<T>(G, Z, tmp, Tr, n, s, sm, 0, false, st));
+        scale_cols_sqrt_kernel<T><<<nblk(n * s), 256, 0, st>>>(Z, n, s, norm2);
+        LD_TRY(check_launch("orthogonal probes"));
+        int stv[2] = {0, 0};
+        LD_CHECK_CUDA(cudaMemcpyAsync(stv, sm.status, sizeof(stv), cudaMemcpyDeviceToHost, st));
+        LD_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (stv[0] || stv[1]) {
+            set_error("orthogonal probes: CholeskyQR2 failed (statuses %d %d)", stv[0], stv[1]);
+            return LD_ERR_NOT_SPD;
+        }
+        return LD_OK;
+    }();
+    a.off = mark;
+    return code;
+}
+template int orthogonal_probes<float>(uint64_t, int64_t, int, int, float *, float *, float *, float *, Arena &,
+                                      cudaStream_t);
+template int orthogonal_probes<double>(uint64_t, int64_t, int, int, double *, double *, double *, double *,
+                                       Arena &, cudaStream_t);
 
 // Apply L^-1 (transpose = false) or L^-T to V (n x c) into W (may alias V).
 // Scratch: Td (r x c fp64), Tt and Ut (r x c, T), part (gemm_tn partials).
@@ -463,7 +530,9 @@ int precond_build(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, int
     clear_error();
     LD_REQUIRE(out != nullptr, "precond_build: out is NULL");
     LD_REQUIRE(n > 0 && X_dev, "precond_build: need n > 0 points");
-    LD_REQUIRE(d >= 1 && d <= 8, "precond_build: d must be in [1, 8]");
+    LD_REQUIRE(d >= 1 && d <= 32, "precond_build: d must be in [1, 32]");
+    LD_REQUIRE(d <= 8 || precision == LD_FP64 || precision == LD_FP32,
+               "precond_build: tensor-core precisions support d <= 8");
     LD_REQUIRE(rank >= 0 && rank <= 1024 && rank <= n, "precond_build: rank must be in [0, min(n, 1024)]");
     LD_REQUIRE(power_iters >= 0 && power_iters <= 64, "precond_build: power_iters in [0, 64]");
     LD_REQUIRE(kern.lengthscale > 0 && kern.variance > 0 && kern.noise >= 0 &&
@@ -473,8 +542,29 @@ int precond_build(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, int
     *out = nullptr;
     cudaStream_t st = (cudaStream_t)stream;
     if (precision == LD_FP64)
-        return build_impl<double>(X_dev, n, d, kern, rank, power_iters, seed, precision, ws, ws_bytes, st, out);
-    return build_impl<float>(X_dev, n, d, kern, rank, power_iters, seed, precision, ws, ws_bytes, st, out);
+        return build_impl<double>(X_dev, n, d, kern, rank, power_iters, seed, precision, 0.0, ws, ws_bytes, st, out);
+    return build_impl<float>(X_dev, n, d, kern, rank, power_iters, seed, precision, 0.0, ws, ws_bytes, st, out);
+}
+
+int precond_build_scaled(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, int32_t rank,
+                         int32_t power_iters, uint64_t seed, double a, int32_t precision, void *ws,
+                         size_t ws_bytes, void *stream, ld_precond **out) {
+    clear_error();
+    LD_REQUIRE(a > 0 && isfinite(a), "precond_build_scaled: a must be > 0");
+    LD_REQUIRE(out != nullptr && n > 0 && X_dev && d >= 1 && d <= 32, "precond_build_scaled: bad arguments");
+    LD_REQUIRE(d <= 8 || precision == LD_FP64 || precision == LD_FP32,
+               "precond_build_scaled: tensor-core precisions support d <= 8");
+    LD_REQUIRE(rank >= 0 && rank <= 1024 && rank <= n && power_iters >= 0 && power_iters <= 64,
+               "precond_build_scaled: bad rank or power_iters");
+    LD_REQUIRE(kern.lengthscale > 0 && kern.variance > 0 && kern.noise >= 0 &&
+                   (kern.kind == LD_RBF || kern.kind == LD_MATERN52),
+               "precond_build_scaled: bad kernel parameters");
+    LD_REQUIRE(precision >= LD_FP64 && precision <= LD_F16X3_TC, "precond_build_scaled: bad precision");
+    *out = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == LD_FP64)
+        return build_impl<double>(X_dev, n, d, kern, rank, power_iters, seed, precision, a, ws, ws_bytes, st, out);
+    return build_impl<float>(X_dev, n, d, kern, rank, power_iters, seed, precision, a, ws, ws_bytes, st, out);
 }
 
 int precond_import(const double *A_host, const double *D_host, int64_t n, int32_t rank,

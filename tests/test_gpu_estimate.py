@@ -115,3 +115,44 @@ def test_converged_tensor_core_accuracy(prec, tol):
                               residual_check=True)
     est, _, _ = estimator.estimate_converged(B, F["logdet_P"], Z.astype(np.float64), 3)
     assert res["logdet"] == pytest.approx(est, rel=tol)
+
+
+def test_slq_by_product_matches_oracle_slq():
+    # Stochastic Lanczos quadrature from the same tridiagonals (fixed t, fp64)
+    n, s, t = 900, 6, 15
+    X, M, A, D, F, B = _problem(n, 3, api.RBF, 0.5, 1e-2, 24, dist="normal")
+    Z = inputs.rademacher(n, s, seed=2)
+    P = api.Precond.import_(A, D, "fp64")
+    res = api.logdet_estimate(cuda(X), api.Kernel(api.RBF, 0.5, 1.0, 1e-2), precond=P, probes=cuda(Z),
+                              order=3, num_probes=s, precision="fp64", fixed_iters=t, max_iters=t)
+    est, _ = estimator.estimate_slq(B, F["logdet_P"], Z.astype(np.float64), t)
+    assert res["slq_logdet"] == pytest.approx(est, rel=1e-10)
+
+
+def test_gaussian_probes_match_oracle():
+    from oracle.splitmix import gaussian_block
+    n, s = 800, 8
+    G = host(api.ld_gaussian(5, n, s, col0=2))
+    np.testing.assert_allclose(G, gaussian_block(5, n, s, col0=2), rtol=1e-13, atol=1e-15)
+    X, M, A, D, F, B = _problem(n, 2, api.MATERN52, 0.3, 5e-2, 16)
+    P = api.Precond.import_(A, D, "fp64")
+    res = api.logdet_estimate(cuda(X), api.Kernel(api.MATERN52, 0.3, 1.0, 5e-2), precond=P, seed=5, order=3,
+                              num_probes=s, probes_per_block=4, precision="fp64", rel_tol=1e-13, max_iters=2000,
+                              probe_kind="gaussian")
+    est, _, _ = estimator.estimate_converged(B, F["logdet_P"], gaussian_block(5, n, s), 3)
+    assert res["logdet"] == pytest.approx(est, rel=1e-10)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+def test_orthogonal_probes_match_oracle(prec, tol):
+    # normal orthogonal probes: CholeskyQR2 on the device vs the oracle's QR, per block
+    from oracle.splitmix import orthogonal_block
+    n, s, ppb = 700, 12, 6
+    X, M, A, D, F, B = _problem(n, 2, api.RBF, 0.25, 2e-2, 16)
+    P = api.Precond.import_(A, D, prec)
+    res = api.logdet_estimate(cuda(X), api.Kernel(api.RBF, 0.25, 1.0, 2e-2), precond=P, seed=7, order=3,
+                              num_probes=s, probes_per_block=ppb, precision=prec, rel_tol=1e-13 if prec == "fp64"
+                              else 1e-6, max_iters=2000, probe_kind="orthogonal")
+    Z = np.concatenate([orthogonal_block(7, n, ppb, col0=b * ppb) for b in range(s // ppb)], axis=1)
+    est, _, _ = estimator.estimate_converged(B, F["logdet_P"], Z, 3)
+    assert res["logdet"] == pytest.approx(est, rel=tol)

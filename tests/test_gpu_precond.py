@@ -71,3 +71,22 @@ def test_build_fp32_is_close_to_oracle():
     Ao, Do = precond.build(M, rademacher_block(2, n, r), q, nu)
     assert ldP == pytest.approx(precond.factors(Ao, Do)["logdet_P"], rel=1e-4)
     assert ldP == pytest.approx(precond.factors(A, D)["logdet_P"], rel=1e-6)
+
+
+def test_diagonal_and_plus_scaling_variants_match_oracle():
+    n, d, r, q, nu = 1000, 2, 24, 2, 2e-2
+    X = inputs.points(n, d, "uniform", seed=4)
+    k = api.Kernel(api.MATERN52, 0.25, 1.0, nu)
+    M = kernels.kernel_matrix(X, api.MATERN52, 0.25, 1.0, nu)
+    # rank 0: P = diag(M) (Appendix "Diagonal")
+    P0 = api.Precond.build(cuda(X), k, 0, precision="fp64")
+    _, D0, ld0 = P0.export()
+    np.testing.assert_allclose(D0, np.diag(M), rtol=1e-15)
+    assert ld0 == pytest.approx(np.sum(np.log(np.diag(M))), rel=1e-14)
+    # plus scaling: P = a I + A A^T with the same sketch
+    Ps = api.Precond.build_scaled(cuda(X), k, r, nu, power_iters=q, seed=2, precision="fp64")
+    A, D, ldP = Ps.export()
+    Ao, Do = precond.build_scaled(M, rademacher_block(2, n, r), q, nu)
+    np.testing.assert_array_equal(D, Do)
+    assert np.abs(A @ A.T - Ao @ Ao.T).max() < 1e-9 * np.abs(Ao @ Ao.T).max()
+    assert ldP == pytest.approx(precond.factors(Ao, Do)["logdet_P"], rel=1e-10)
