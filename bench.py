@@ -30,7 +30,7 @@ WORKLOAD = "matern_n1048576_d4"
 METRIC = "log det estimates/sec at n=2^20 (Matern-5/2, d=4, r_3, rank 512, 16 probes, t=20)"
 UNIT = "estimates/s"
 
-# GB300 ALU roofline for the kernel product (derivation in the design doc): per SM and
+# GB300 ALU roofline for the kernel product: per SM and
 # clock, 128 fp32 lane-ops, 32 MUFU ex2 and 16 MUFU sqrt; 152 SMs at 2070 MHz.
 # Algorithmic work per pair (i, j): Matern-5/2 d coordinate differences and
 # squares, two FMAs of the polynomial and one product (2d + 3 fp32 ops), one
@@ -48,6 +48,29 @@ def pair_peak_gps(kind, d):
     return SMS * per_clk * SM_MHZ_MAX * 1e6 / 1e9
 
 
+def rank_probe_seed(rank):
+    """Probe seed of one rank: every rank estimates with probes of its own, so the
+    ranks' estimates are independent units of work (no data-path collective)."""
+    from paper_2405_03474_gb300 import inputs
+    return inputs.SEED_PROBES + 1000 * rank
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: the job ends when its last rank ends."""
+    if world == 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, ms_max):
+    """Whole-job throughput: every rank completes `steps` estimates in ms_max."""
+    return world * steps / (ms_max / 1e3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -60,6 +83,8 @@ def parse():
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-precision-compare", action="store_true",
+                    help="skip the one-launch-per-precision product comparison after the timed region")
     ap.add_argument("--kz-only", type=int, default=0, metavar="C",
                     help="profiling aid: run only the kernel product on C columns (2 warm-up + 1 launch)")
     return ap.parse_args()
@@ -86,15 +111,15 @@ def _attach(names):
 
 
 def _oracle_rows(job):
-    """Worker: seconds the oracle's matrix-free rows of (K + nu I) V take."""
+    """Worker: the oracle's matrix-free rows of (K + nu I) V and the seconds they take."""
     rows, ncols, ell, nu = job
     import numpy as np
     from oracle import kernels
     X = _SH["X"][1]
     V = _SH["V%d" % ncols][1]
     t0 = time.perf_counter()
-    kernels.kz_rows(X, V, np.asarray(rows), kernels.MATERN52, ell, 1.0, nu)
-    return time.perf_counter() - t0
+    out = kernels.kz_rows(X, V, np.asarray(rows), kernels.MATERN52, ell, 1.0, nu)
+    return time.perf_counter() - t0, out
 
 
 class OraclePool:
@@ -139,10 +164,17 @@ class OraclePool:
         n = w["n"]
         per_pass = {}
         sample_rows = rows_per_core * self.cores
+        import numpy as np
+        stride = max(1, n // sample_rows)  # rows spread over the whole point set
         for ncols in self.cols:
-            jobs = [(list(range(c * rows_per_core, (c + 1) * rows_per_core)), ncols, w["lengthscale"],
+            jobs = [([(c * rows_per_core + k) * stride for k in range(rows_per_core)], ncols, w["lengthscale"],
                      w["noise"]) for c in range(self.cores)]
-            per_pass[ncols] = max(self.pool.map(_oracle_rows, jobs)) * n / sample_rows
+            got = self.pool.map(_oracle_rows, jobs)
+            per_pass[ncols] = max(g[0] for g in got) * n / sample_rows
+            if ncols == w["probes"]:
+                # the sampled rows double as the FP64 reference of the product's error
+                self.rows = np.concatenate([j[0] for j in jobs])
+                self.values = np.concatenate([g[1] for g in got])
         total = ((w["power_iters"] + 2) * per_pass[w["rank"]] + t_steps * per_pass[w["probes"]]
                  + per_pass[w["probes"] * w["order"]])
         sample = ("oracle kernels.kz_rows on %d of %d rows for V with %s columns, %d processes x 1 "
@@ -228,7 +260,7 @@ def run_ours(args, rank, world, local_rank, pool):
     X = X_host.to(dev)
     opts = dict(order=w["order"], num_probes=w["probes"], probes_per_block=w["probes"],
                 fixed_iters=args.t, max_iters=args.t, precision=args.precision, residual_check=True,
-                seed=inputs.SEED_PROBES + 1000 * rank)
+                seed=rank_probe_seed(rank))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def step(Xd):
@@ -272,11 +304,8 @@ def run_ours(args, rank, world, local_rank, pool):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms_max = float(t.item())
-    value = world * args.steps / (total_ms_max / 1e3)
+    total_ms_max = max_over_ranks(total_ms, world, dev)
+    value = job_value(world, args.steps, total_ms_max)
 
     # end to end through the public API: host points in, host result out
     e2e = None
@@ -293,29 +322,12 @@ def run_ours(args, rank, world, local_rank, pool):
             b.record(stream)
             torch.cuda.synchronize()
             e2e_ms.append(a.elapsed_time(b))
-        tt = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * args.steps / (float(tt.item()) / 1e3), "unit": UNIT,
+        e2e = {"value": job_value(world, args.steps, max_over_ranks(sum(e2e_ms), world, dev)), "unit": UNIT,
                "h2d_bytes_per_step": int(X_host.numel() * X_host.element_size()),
                "d2h_bytes_per_step": int(8 * (w["probes"] + 16))}
 
     if rank != 0:
         return None
-
-    # sampled-row error of the kernel product against the oracle (same V)
-    err = None
-    try:
-        from oracle import kernels
-        c = w["probes"]
-        V = inputs.gaussian(n, c, seed=7)
-        Wg = api.ld_kz(X, torch.as_tensor(V, dtype=torch.float32).to(dev), kern, args.precision).cpu().numpy()
-        rows = np.random.default_rng(0).choice(n, 8, replace=False)
-        ref = kernels.kz_rows(inputs.points(n, d, w["dist"], seed=inputs.SEED_POINTS), V, rows, w["kind"],
-                              w["lengthscale"], w["variance"], w["noise"])
-        err = float(np.linalg.norm(Wg[rows] - ref) / np.linalg.norm(ref))
-    except Exception as ex:  # report, do not hide
-        err = "failed: %s" % ex
 
     avg_launch_ms = kz_ms.value / max(1, kz_n.value)
     pairs_per_launch = kz_pairs.value / max(1, kz_n.value)
@@ -337,7 +349,6 @@ def run_ours(args, rank, world, local_rank, pool):
                                / (total_ms_max / 1e3),
         "estimate": {"logdet": res["logdet"], "logdet_P": res["logdet_P"], "std_err": res["std_err"],
                      "iters": res["iters"], "max_resid": res["max_resid"][:w["order"]]},
-        "kz_rel_err_vs_oracle_sampled_rows": err,
         "roofline": {"kernel": "kz_tc_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
                      "launches": kz_n.value, "avg_launch_ms": avg_launch_ms,
@@ -351,6 +362,32 @@ def run_ours(args, rank, world, local_rank, pool):
         sec, sample = pool.estimate_seconds(args.t)
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
                                 "sample": sample}
+        # error of the timed product (hi/lo fp16 tensor cores, 16 columns) on the rows the
+        # baseline computed in FP64, same V
+        V = torch.as_tensor(inputs.gaussian(n, w["probes"], seed=5), dtype=torch.float32).to(dev)
+        Wg = api.ld_kz(X, V, kern, args.precision)[torch.as_tensor(pool.rows, device=dev)].double().cpu().numpy()
+        line["kz_rel_err_vs_fp64_oracle"] = {
+            "value": float(np.linalg.norm(Wg - pool.values) / np.linalg.norm(pool.values)),
+            "rows": int(len(pool.rows)), "columns": w["probes"], "precision": args.precision}
+        # the same product in every precision (one launch each, after the timed region):
+        # time and error on the same FP64 rows, i.e. the speedup at a stated accuracy
+        if not args.no_precision_compare:
+            cmp = {}
+            idx = torch.as_tensor(pool.rows, device=dev)
+            for prec in ("fp32", "f16x3_tc", "f16_tc", "bf16_tc"):
+                api.ld_kz(X, V, kern, prec)  # warm (workspace, first-launch costs)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                Wp = api.ld_kz(X, V, kern, prec)
+                b.record(stream)
+                torch.cuda.synchronize()
+                Wr = Wp[idx].double().cpu().numpy()
+                cmp[prec] = {"ms": a.elapsed_time(b),
+                             "rel_err": float(np.linalg.norm(Wr - pool.values) / np.linalg.norm(pool.values))}
+            for prec in cmp:
+                cmp[prec]["speedup_vs_fp32"] = cmp["fp32"]["ms"] / cmp[prec]["ms"]
+            line["kz_precision_compare"] = {"columns": w["probes"], "n": n, **cmp}
     return line
 
 
