@@ -62,3 +62,22 @@ def gaussian_block(seed, n, s, col0=0):
     u1 = uniform_open(seed, np.uint64(2) * k)
     u2 = uniform_open(seed, np.uint64(2) * k + np.uint64(1))
     return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+ORF_NORM_COL0 = 1 << 30
+
+
+def orthogonal_block(seed, n, s, col0=0):
+    """n-by-s block of normal orthogonal probes (the Appendix's probe type, an
+    application of Orthogonal Monte Carlo, Yu et al. 2016): W = S Q.
+
+    Reading: Q has the orthonormal columns of the QR factorisation, R's diagonal
+    taken positive, of the Gaussian block of columns col0 .. col0+s-1 (a Haar
+    distributed set of s orthonormal vectors); S is diagonal with chi_n entries,
+    column c's being the Euclidean norm of the Gaussian column
+    ORF_NORM_COL0 + col0 + c of the same stream.  Requires s <= n."""
+    G = gaussian_block(seed, n, s, col0)
+    Q, R = np.linalg.qr(G)
+    Q = Q * np.sign(np.diag(R))
+    H = gaussian_block(seed, n, s, ORF_NORM_COL0 + col0)
+    return Q * np.sqrt(np.einsum("ij,ij->j", H, H))

@@ -1,5 +1,6 @@
 """Pins for oracle/splitmix.py against the published SplitMix64 sequence."""
 import numpy as np
+import pytest
 
 from oracle import splitmix
 
@@ -56,3 +57,45 @@ def test_gaussian_block_is_standard_normal():
     u2 = (float(int(splitmix.splitmix64(9, [2 * k + 1])[0]) >> 11) + 0.5) * 2.0 ** -53
     import math
     assert Z[123, 1] == math.sqrt(-2 * math.log(u1)) * math.cos(2 * math.pi * u2)
+
+
+def test_orthogonal_block_structure():
+    # columns mutually orthogonal, each of squared norm |h_c|^2 (h_c the chi_n column),
+    # and Z^T G upper triangular with a positive diagonal (Q is G's QR factor, not
+    # another orthonormal basis of its span)
+    n, s = 300, 12
+    Z = splitmix.orthogonal_block(4, n, s, col0=5)
+    G = splitmix.gaussian_block(4, n, s, col0=5)
+    H = splitmix.gaussian_block(4, n, s, col0=splitmix.ORF_NORM_COL0 + 5)
+    gram = Z.T @ Z
+    h2 = (H ** 2).sum(axis=0)
+    np.testing.assert_allclose(np.diag(gram), h2, rtol=1e-12)
+    off = gram - np.diag(np.diag(gram))
+    assert np.abs(off).max() < 1e-11 * h2.max()
+    ZG = Z.T @ G
+    assert np.abs(np.tril(ZG, -1)).max() < 1e-10 * np.abs(ZG).max()
+    assert (np.diag(ZG) > 0).all()
+    # G lies in the span of Z
+    coef = np.linalg.lstsq(Z, G, rcond=None)[0]
+    np.testing.assert_allclose(Z @ coef, G, atol=1e-10)
+
+
+def test_orthogonal_block_complete_basis_gives_exact_trace():
+    # with s = n the directions form an orthonormal basis: sum_c z_c^T A z_c / |z_c|^2 = tr A
+    n = 40
+    Z = splitmix.orthogonal_block(8, n, n)
+    A = np.random.default_rng(0).standard_normal((n, n))
+    A = A + A.T
+    val = sum(Z[:, c] @ A @ Z[:, c] / (Z[:, c] @ Z[:, c]) for c in range(n))
+    assert val == pytest.approx(np.trace(A), abs=1e-10)
+
+
+def test_orthogonal_block_marginals_are_standard_normal():
+    # each column is marginally N(0, I_n): moments over many blocks, and
+    # E |z|^2 = n (chi_n squared)
+    from scipy import stats
+    n, s = 64, 16
+    Z = np.concatenate([splitmix.orthogonal_block(3, n, s, col0=s * b) for b in range(200)], axis=1)
+    assert stats.kstest(Z.ravel(), "norm").pvalue > 1e-3
+    assert abs(Z.mean()) < 0.01 and abs(Z.var() - 1.0) < 0.01
+    assert abs((Z ** 2).sum(axis=0).mean() / n - 1.0) < 0.02
