@@ -1,5 +1,6 @@
-// Symmetric tensor-core kernel product W = (K + noise I) V for up to 16 columns
-// (the CG passes: one column per probe), evaluating each kernel value once.
+// Symmetric tensor-core kernel product W = (K + noise I) V for up to 48 columns
+// (the CG passes: one column per probe; the residual pass: probes x shifts),
+// evaluating each kernel value once.
 //
 // K is symmetric, so the 128 x 128 block K_IJ serves two products: W_I += K_IJ V_J
 // and W_J += K_IJ^T V_I.  The CTA owning row block I visits the blocks
@@ -10,13 +11,17 @@
 //     differences and polynomial, one MUFU sqrt + ex2 per pair, fp16 hi/lo);
 //   * the MMA thread issues D_I += K_IJ V_J (K-major A: rows i, K = j) and
 //     D'_J = K_IJ^T V_I (the same shared tile read as an MN-major A: rows j, K = i);
-//   * two blocks later the eval warps read D'_J from tensor memory, stage it in
-//     shared memory and add it into W_J with one cp.reduce.async.bulk .add.f32.
+//   * two blocks later the eval warps read D'_J from tensor memory (the load is
+//     issued before the next tile's evaluation and completed after it) and add it
+//     into W_J, each thread one 16-byte vector reduction (red.global.add.v4.f32)
+//     of 4 columns of one row.
 // W is zeroed first and every contribution (including the owner's own rows and
 // the noise term, at the end) is added, so the order of additions across CTAs is
 // the only run-to-run difference (fp32 rounding).  D_I is accumulated in tensor
 // memory in chunks of 4 blocks and drained to fp32 round-to-nearest partial
-// sums, as in the non-symmetric kernel.  Every mbarrier wait is bounded.
+// sums, held in registers (each eval thread owns a quarter of one row's columns),
+// as in the non-symmetric kernel.  The kernel is compiled for SN = 16 and SN = 48
+// columns (padded).  Every mbarrier wait is bounded.
 #include <math.h>
 
 #include <algorithm>
@@ -35,59 +40,73 @@ constexpr int SNEVAL = 16;                  // eval warps
 constexpr int SNTHREADS = (SNEVAL + 2) * 32;
 constexpr int HALF_TILE = BR * BR * 2;      // one 128 x 128 tile of halves (32 KB)
 constexpr int SKCH = 4;                     // blocks per TMEM chunk before a drain (hi/lo)
-constexpr int SYM_N = 16;                   // MMA N (columns, padded)
 constexpr int CORE_SBO = (BR / 8) * 128;    // 2048: byte step between 8-row groups
+constexpr int SN_MAX = 48;
 
 struct SymParams {
     const float *Xp;     // per 128-point tile: d x 128 floats, far-padded, log2 e folded in
-    const uint8_t *img;  // per 128-point tile: nprod x (16 x 128) halves, canonical K-major
+    const uint8_t *img;  // per 128-point tile: nprod x (SN x 128) halves, canonical K-major
     const float *V;      // n x c
-    const float *colinv; // 1 / column scale (16)
+    const float *colinv; // 1 / column scale (SN)
     float *W;            // zeroed; every contribution is added
     int64_t n;
-    int d, c, NB, ncols_tmem, bulk_ok;
+    int d, c, NB, ncols_tmem, vec_ok;
     float variance, noise;
     int *err;
 };
 
 struct SymLayout {
-    int sl, a_bytes, b_bytes, x_bytes, l_bytes, st_bytes;
-    int a_off, l_off, vi_off, st_off, acc_off, total;
+    int sl, a_bytes, b_bytes, x_bytes, l_bytes;
+    int a_off, l_off, vi_off, total;
 };
 
-SymLayout make_sym_layout(int d, int nprod, int c, int sl) {
+inline int round1k(int b) { return ((b + 1023) / 1024) * 1024; }
+
+SymLayout make_sym_layout(int sn, int d, int nprod, int sl) {
     SymLayout L;
     L.sl = sl;
     L.a_bytes = (nprod == 3 ? 2 : 1) * HALF_TILE;
-    L.b_bytes = (nprod == 3 ? 2 : 1) * SYM_N * BR * 2;
+    L.b_bytes = (nprod == 3 ? 2 : 1) * sn * BR * 2;
     L.x_bytes = BR * d * 4;
-    L.l_bytes = ((L.b_bytes + L.x_bytes + 1023) / 1024) * 1024;
-    L.st_bytes = ((BR * c * 4 + 1023) / 1024) * 1024;
+    L.l_bytes = round1k(L.b_bytes + L.x_bytes);
     L.a_off = 1024;
     L.l_off = L.a_off + 2 * L.a_bytes;
     L.vi_off = L.l_off + sl * L.l_bytes;
-    L.st_off = L.vi_off + ((L.b_bytes + 1023) / 1024) * 1024;
-    L.acc_off = L.st_off + 2 * L.st_bytes;
-    const int acc = nprod == 3 ? BR * (SYM_N + 1) * 4 : 0;
-    L.total = L.acc_off + acc + 1024;
+    L.total = L.vi_off + round1k(L.b_bytes) + 1024;
     return L;
 }
 
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *v) {
-    uint32_t r[4];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = __uint_as_float(r[q]);
+int sym_stages(int sn, int d, int nprod) {
+    for (int s = 4; s >= 2; --s)
+        if (make_sym_layout(sn, d, nprod, s).total <= 225 * 1024) return s;
+    return 0;
 }
 
-__device__ __forceinline__ void eval_barrier() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+// Asynchronous TMEM loads of G x 4 columns (32 lanes): issue, then wait before use.  The
+// wait names the destination registers so no use is scheduled ahead of it.
+template <int G>
+__device__ __forceinline__ void tmem_ld_issue(uint32_t taddr, uint32_t (&r)[4 * G]) {
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(r[4 * g]), "=r"(r[4 * g + 1]), "=r"(r[4 * g + 2]), "=r"(r[4 * g + 3])
+                     : "r"(taddr + 4u * g));
+}
+template <int G>
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[4 * G], uint32_t (&t)[4 * G]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 4 * G; ++q) asm volatile("" : "+r"(r[q]), "+r"(t[q]));
+}
 
-template <int KIND, int DC, int NPROD, bool BF16>
+template <int KIND, int DC, int NPROD, bool BF16, int SN>
 __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLayout L) {
     constexpr bool DRAIN = NPROD == 3;
+    constexpr int CPT = SN / 4;   // columns per eval thread (a quarter of a row)
+    constexpr int G4 = CPT / 4;   // groups of 4 columns per thread
+    // the D' load is issued before the next tile's evaluation and completed after it
+    // when its registers fit beside the evaluation's (16 columns)
+    constexpr bool ASYNC_T = SN == 16;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);  // [sl]
@@ -105,8 +124,8 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
     uint8_t *abase = smem + L.a_off;
     uint8_t *lbase = smem + L.l_off;
     uint8_t *vimg = smem + L.vi_off;
-    float *stage_f = reinterpret_cast<float *>(smem + L.st_off);
-    float *sacc = reinterpret_cast<float *>(smem + L.acc_off);
+    // variance / column scale per column, read at each drain (not held in registers)
+    float *s_cscale = reinterpret_cast<float *>(smem + 512);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -115,8 +134,11 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
     const int NB = p.NB, H = NB / 2;
     const int T = (NB & 1) ? H + 1 : (I < H ? H + 1 : H);  // blocks J = (I + b) % NB
     const int SL = L.sl;
-    const int N = SYM_N;
-    const uint32_t doff = DRAIN ? 2 * N : N;  // TMEM columns of the two D' buffers
+    // With the hi/lo split an accumulator is 2 SN columns wide: [K_hi V_hi | K_hi V_lo + K_lo V_hi]
+    // (one N = 2 SN MMA reads the K_hi tile once for both V halves); the halves are summed when
+    // drained.  D ping-pong (drained) or single D, then the two D' buffers.
+    constexpr uint32_t NW = NPROD == 3 ? 2 * SN : SN;
+    const uint32_t doff = DRAIN ? 2 * NW : NW;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < SL; ++s) {
@@ -134,11 +156,10 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
         mbar_init(vfull, 1);
         mbar_init(done, 1);
         *s_err = 0;
+        for (int q = 0; q < SN; ++q) s_cscale[q] = p.variance * p.colinv[q];
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_smem();
     }
-    if (DRAIN)
-        for (int e = threadIdx.x; e < BR * (N + 1); e += SNTHREADS) sacc[e] = 0.f;
     if (warp == SNEVAL) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(p.ncols_tmem)
@@ -158,8 +179,8 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
             mbar_expect_tx(vfull, bb);
             bulk_g2s(vimg, p.img + (size_t)I * bb, bb, vfull);
             int b = 0;
-            for (; b < T; ++b) {
-                const int J = (I + b) % NB;
+            int J = I;
+            for (; b < T; ++b, J = (J + 1 == NB) ? 0 : J + 1) {
                 const int s = b % SL;
                 if (b >= SL && !mbar_wait(&empty[s], ((b / SL) - 1) & 1)) {
                     atomicOr(s_err, ERR_TIMEOUT);
@@ -177,16 +198,17 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
     } else if (warp == SNEVAL) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = make_idesc(BR, N, BF16 ? 1u : 0u, 0u);
-            const uint32_t idesc_t = make_idesc(BR, N, BF16 ? 1u : 0u, 1u);  // A read MN-major
-            const uint32_t bhalf = (uint32_t)(N * BR * 2);
+            const uint32_t idesc = make_idesc(BR, SN, BF16 ? 1u : 0u, 0u);
+            const uint32_t idesc_t = make_idesc(BR, SN, BF16 ? 1u : 0u, 1u);  // A read MN-major
+            const uint32_t idesc_w = make_idesc(BR, (int)NW, BF16 ? 1u : 0u, 0u);  // B = [V_hi | V_lo]
+            const uint32_t idesc_wt = make_idesc(BR, (int)NW, BF16 ? 1u : 0u, 1u);
             bool ok = mbar_wait(vfull, 0);
             const uint32_t vi0 = smem_u32(vimg);
             for (int b = 0; b < T && ok; ++b) {
                 const int s = b % SL, sa = b & 1;
                 const int k = b / SKCH;
                 const bool first = DRAIN ? (b % SKCH == 0) : (b == 0);
-                const uint32_t dt = tmem + (DRAIN ? (uint32_t)((k & 1) * N) : 0u);
+                const uint32_t dt = tmem + (DRAIN ? (uint32_t)((k & 1) * NW) : 0u);
                 if (DRAIN && first && k >= 2 && !mbar_wait(&cempty[k & 1], ((k - 2) >> 1) & 1)) {
                     ok = false;
                     break;
@@ -207,31 +229,27 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
                 for (int ks = 0; ks < BR / 16; ++ks) {
                     const uint32_t koff = (uint32_t)ks * 256u;
                     const uint64_t ah = make_desc(a0 + koff, 128, CORE_SBO);
-                    const uint64_t bh = make_desc(b0 + koff, 128, CORE_SBO);
-                    mma_f16(dt, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
+                    const uint64_t bh = make_desc(b0 + koff, 128, CORE_SBO);  // N = NW spans hi, lo
+                    mma_f16(dt, ah, bh, idesc_w, (first && ks == 0) ? 0u : 1u);
                     if (NPROD == 3) {
                         const uint64_t al = make_desc(a0 + (uint32_t)HALF_TILE + koff, 128, CORE_SBO);
-                        const uint64_t bl = make_desc(b0 + bhalf + koff, 128, CORE_SBO);
-                        mma_f16(dt, ah, bl, idesc, 1u);
-                        mma_f16(dt, al, bh, idesc, 1u);
+                        mma_f16(dt + SN, al, bh, idesc, 1u);
                     }
                 }
                 if (b >= 1) {
                     // D'_J = K_IJ^T V_I: the same tile MN-major (rows j; lbo = 2048 along i,
                     // sbo = 128 along j), B = own V image (K = i)
-                    const uint32_t tdt = tmem + doff + (uint32_t)((b & 1) * N);
+                    const uint32_t tdt = tmem + doff + (uint32_t)((b & 1) * NW);
 #pragma unroll
                     for (int ks = 0; ks < BR / 16; ++ks) {
                         const uint32_t koff_t = (uint32_t)ks * (2u * CORE_SBO);
                         const uint32_t bkoff = (uint32_t)ks * 256u;
                         const uint64_t ah = make_desc(a0 + koff_t, CORE_SBO, 128);
                         const uint64_t bh = make_desc(vi0 + bkoff, 128, CORE_SBO);
-                        mma_f16(tdt, ah, bh, idesc_t, ks == 0 ? 0u : 1u);
+                        mma_f16(tdt, ah, bh, idesc_wt, ks == 0 ? 0u : 1u);
                         if (NPROD == 3) {
                             const uint64_t al = make_desc(a0 + (uint32_t)HALF_TILE + koff_t, CORE_SBO, 128);
-                            const uint64_t bl = make_desc(vi0 + bhalf + bkoff, 128, CORE_SBO);
-                            mma_f16(tdt, ah, bl, idesc_t, 1u);
-                            mma_f16(tdt, al, bh, idesc_t, 1u);
+                            mma_f16(tdt + SN, al, bh, idesc_t, 1u);
                         }
                     }
                     mma_commit(&tfull[b & 1]);
@@ -250,9 +268,10 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
         const int rg = lane;
         const int kq = warp;
         const int quad = warp & 3;       // TMEM lane quadrant
-        const int part = warp >> 2;      // 4 columns of the 16 in drains / epilogue
-        const int c4 = part * 4;
+        const int part = warp >> 2;      // a quarter of the columns in drains / epilogue
+        const int c0 = part * CPT;
         const int row = quad * 32 + lane;
+        const uint32_t tlane = (uint32_t)(quad * 32) << 16;
         float2 xr[4][8];
         {
             const float *tile = p.Xp + (size_t)I * BR * dd;
@@ -264,60 +283,73 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
                     xr[k][a] = make_float2(v, v);
                 }
         }
-        float cscale[4];
+        const float *cscale = s_cscale + c0;
+        float acc[CPT];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) cscale[q] = p.variance * p.colinv[c4 + q];
+        for (int q = 0; q < CPT; ++q) acc[q] = 0.f;
 
         // Waits of the eval threads never leave the loop: after the first timeout (error
-        // word set) every later wait is skipped, so all 512 threads keep running the
-        // same sequence of named barriers and finish quickly.
+        // word set) every later wait is skipped and nothing more is added to W, so all
+        // threads finish quickly.
         auto wait_ok = [&](uint64_t *bar, uint32_t parity) {
             if (*reinterpret_cast<volatile int *>(s_err)) return;
             if (!mbar_wait(bar, parity)) atomicOr(s_err, ERR_TIMEOUT);
         };
-        // D chunk k -> fp32 partial sums
+        // D chunk k -> fp32 partial sums in registers
         auto drain_d = [&](int k) {
             wait_ok(&cfull[k & 1], (k >> 1) & 1);
             tc_fence_after();
-            float v[4];
-            tmem_ld4(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((k & 1) * N + c4), v);
+            uint32_t h[CPT], l[CPT];
+            const uint32_t ta = tmem + tlane + (uint32_t)((k & 1) * NW + c0);
+            tmem_ld_issue<G4>(ta, h);
+            tmem_ld_issue<G4>(ta + SN, l);
+            tmem_ld_wait<G4>(h, l);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) sacc[row * (N + 1) + c4 + q] += v[q];
+            for (int q = 0; q < CPT; ++q) acc[q] += __uint_as_float(h[q]) + __uint_as_float(l[q]);
             tc_fence_before();
             mbar_arrive(&cempty[k & 1]);
         };
-        // D' of block bb -> W rows of block J = (I + bb) % NB (added)
-        auto drain_t = [&](int bb) {
-            if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        // Add CPT values of one W row (columns c0 ..): 16-byte vector reductions when rows
+        // are 16-byte aligned, else per element.
+        auto add_row = [&](int64_t grow, const float (&val)[CPT]) {
+            float *dst = p.W + grow * p.c + c0;
+            if (p.vec_ok) {
+#pragma unroll
+                for (int g = 0; g < G4; ++g)
+                    if (c0 + 4 * g < p.c)
+                        atomicAdd(reinterpret_cast<float4 *>(dst + 4 * g),
+                                  make_float4(val[4 * g], val[4 * g + 1], val[4 * g + 2], val[4 * g + 3]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < CPT; ++q)
+                    if (c0 + q < p.c) atomicAdd(dst + q, val[q]);
+            }
+        };
+        // D' of block bb -> W rows of block J = (I + bb) % NB
+        uint32_t tr[CPT], tl[CPT];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) tr[q] = tl[q] = 0u;
+        auto drain_t_issue = [&](int bb) {
             wait_ok(&tfull[bb & 1], ((bb - 1) >> 1) & 1);
             tc_fence_after();
-            float v[4];
-            tmem_ld4(tmem + ((uint32_t)(quad * 32) << 16) + doff + (uint32_t)((bb & 1) * N + c4), v);
+            const uint32_t ta = tmem + tlane + doff + (uint32_t)((bb & 1) * NW + c0);
+            tmem_ld_issue<G4>(ta, tr);
+            if (NPROD == 3) tmem_ld_issue<G4>(ta + SN, tl);
+        };
+        auto drain_t_finish = [&](int bb) {
+            tmem_ld_wait<G4>(tr, tl);
             tc_fence_before();
             mbar_arrive(&tempty[bb & 1]);
-            const int J = (I + bb) % NB;
+            int J = I + bb;
+            if (J >= NB) J -= NB;
             const int64_t r0 = (int64_t)J * BR;
-            const int rows_valid = (int)std::min<int64_t>(BR, p.n - r0);
-            if (p.bulk_ok && rows_valid == BR) {  // uniform over the eval threads
-                float *stg = stage_f + (size_t)(bb & 1) * (L.st_bytes / 4);
-                eval_barrier();  // staging free: thread 0 waited for the last bulk read above
+            if (r0 + row < p.n && !*reinterpret_cast<volatile int *>(s_err)) {
+                float val[CPT];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (c4 + q < p.c) stg[row * p.c + c4 + q] = v[q] * cscale[q];
-                fence_async_smem();
-                eval_barrier();
-                if (threadIdx.x == 0 && !*reinterpret_cast<volatile int *>(s_err)) {
-                    asm volatile(
-                        "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
-                            p.W + r0 * p.c),
-                        "r"(smem_u32(stg)), "r"((uint32_t)(BR * p.c * 4))
-                        : "memory");
-                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-                }
-            } else if (row < rows_valid) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (c4 + q < p.c) atomicAdd(p.W + (r0 + row) * p.c + c4 + q, v[q] * cscale[q]);
+                for (int q = 0; q < CPT; ++q)
+                    val[q] = (NPROD == 3 ? __uint_as_float(tr[q]) + __uint_as_float(tl[q]) : __uint_as_float(tr[q])) *
+                             cscale[q];
+                add_row(r0 + row, val);
             }
         };
 
@@ -326,7 +358,10 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
         for (int b = 0; b < T; ++b) {
             const int s = b % SL, sa = b & 1;
             if (DRAIN && b % SKCH == SKCH / 2 && b >= SKCH + SKCH / 2) drain_d(drained++);
-            if (b >= 3) drain_t(b - 2);
+            if (b >= 3) {
+                drain_t_issue(b - 2);
+                if (!ASYNC_T) drain_t_finish(b - 2);
+            }
             wait_ok(&full[s], (b / SL) & 1);
             if (b >= 2) wait_ok(&aempty[sa], ((b >> 1) - 1) & 1);
             uint8_t *ast = abase + (size_t)sa * L.a_bytes;
@@ -375,56 +410,44 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
                 }
             }
             fence_async_smem();
+            // D' buffer (b - 2) & 1 is released before this tile's MMA needs it
+            if (ASYNC_T && b >= 3) drain_t_finish(b - 2);
             mbar_arrive(&afull[sa]);
         }
         // ---------------- tail: remaining transposed blocks, D chunks, own rows
         wait_ok(done, 0);
         tc_fence_after();
-        for (int bb = std::max(1, T - 2); bb < T; ++bb) drain_t(bb);
+        for (int bb = std::max(1, T - 2); bb < T; ++bb) {
+            drain_t_issue(bb);
+            drain_t_finish(bb);
+        }
         if (DRAIN)
             for (; drained < C; ++drained) drain_d(drained);
         {
-            float v[4];
+            float v[CPT];
             if (DRAIN) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) v[q] = sacc[row * (N + 1) + c4 + q];
+                for (int q = 0; q < CPT; ++q) v[q] = acc[q];
             } else {
-                tmem_ld4(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c4, v);
+                uint32_t h[CPT], l[CPT];
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) l[q] = 0u;
+                tmem_ld_issue<G4>(tmem + tlane + (uint32_t)c0, h);
+                tmem_ld_wait<G4>(h, l);
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) v[q] = __uint_as_float(h[q]);
             }
             const int64_t r0 = (int64_t)I * BR;
-            const int rows_valid = (int)std::min<int64_t>(BR, p.n - r0);
-            float outv[4];
+            if (r0 + row < p.n && !*reinterpret_cast<volatile int *>(s_err)) {
+                float outv[CPT];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int col = c4 + q;
-                outv[q] = (row < rows_valid && col < p.c)
-                              ? v[q] * cscale[q] + p.noise * p.V[(r0 + row) * p.c + col]
-                              : 0.f;
-            }
-            if (p.bulk_ok && rows_valid == BR) {
-                if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                eval_barrier();
-                float *stg = stage_f;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (c4 + q < p.c) stg[row * p.c + c4 + q] = outv[q];
-                fence_async_smem();
-                eval_barrier();
-                if (threadIdx.x == 0 && !*reinterpret_cast<volatile int *>(s_err)) {
-                    asm volatile(
-                        "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
-                            p.W + r0 * p.c),
-                        "r"(smem_u32(stg)), "r"((uint32_t)(BR * p.c * 4))
-                        : "memory");
-                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                for (int q = 0; q < CPT; ++q) {
+                    const int col = c0 + q;
+                    outv[q] = col < p.c ? v[q] * cscale[q] + p.noise * p.V[(r0 + row) * p.c + col] : 0.f;
                 }
-            } else if (row < rows_valid) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (c4 + q < p.c) atomicAdd(p.W + (r0 + row) * p.c + c4 + q, outv[q]);
+                add_row(r0 + row, outv);
             }
         }
-        if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
@@ -449,13 +472,13 @@ __global__ void sym_point_tiles_kernel(const float *Xs, int64_t n, int d, float 
     Xp[idx] = i < n ? Xs[i * d + a] * factor : 1e18f;
 }
 
-// V operand image per 128-point tile: 16 columns x 128 K values, canonical K-major
+// V operand image per 128-point tile: SN columns x 128 K values, canonical K-major
 // (byte offset (col/8)*2048 + (jj/8)*128 + (col%8)*16 + (jj%8)*2), hi then lo.
 template <bool BF16, int NPROD>
-__global__ void sym_image_kernel(const float *V, int64_t n, int c, int ntiles, const float *scale,
+__global__ void sym_image_kernel(const float *V, int64_t n, int c, int sn, int ntiles, const float *scale,
                                  uint8_t *img) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t per_tile = (int64_t)SYM_N * (BR / 8);
+    const int64_t per_tile = (int64_t)sn * (BR / 8);
     if (idx >= per_tile * ntiles) return;
     const int64_t t = idx / per_tile;
     const int rem = (int)(idx % per_tile);
@@ -473,7 +496,7 @@ __global__ void sym_image_kernel(const float *V, int64_t n, int c, int ntiles, c
     uint4 hi;
     hi.x = pack2<BF16>(v[0], v[1]); hi.y = pack2<BF16>(v[2], v[3]);
     hi.z = pack2<BF16>(v[4], v[5]); hi.w = pack2<BF16>(v[6], v[7]);
-    const size_t tile_bytes = (size_t)(NPROD == 3 ? 2 : 1) * SYM_N * BR * 2;
+    const size_t tile_bytes = (size_t)(NPROD == 3 ? 2 : 1) * sn * BR * 2;
     uint8_t *base = img + (size_t)t * tile_bytes;
     const size_t off = (size_t)g * CORE_SBO + (size_t)kq * 128 + (size_t)cr * 16;
     *reinterpret_cast<uint4 *>(base + off) = hi;
@@ -485,11 +508,11 @@ __global__ void sym_image_kernel(const float *V, int64_t n, int c, int ntiles, c
             const float2 f = unpack2<BF16>(hp[w]);
             lp[w] = pack2<BF16>(v[2 * w] - f.x, v[2 * w + 1] - f.y);
         }
-        *reinterpret_cast<uint4 *>(base + (size_t)SYM_N * BR * 2 + off) = lo;
+        *reinterpret_cast<uint4 *>(base + (size_t)sn * BR * 2 + off) = lo;
     }
 }
 
-__global__ void sym_colmax_kernel(const float *V, int64_t n, int c, float *part) {
+__global__ void sym_colmax_kernel(const float *V, int64_t n, int c, int sn, float *part) {
     const int col = threadIdx.x;
     const int nb = gridDim.x;
     const int64_t per = (n + nb - 1) / nb;
@@ -497,14 +520,14 @@ __global__ void sym_colmax_kernel(const float *V, int64_t n, int c, float *part)
     float m = 0.f;
     if (col < c)
         for (int64_t i = r0; i < r1; ++i) m = fmaxf(m, fabsf(V[i * c + col]));
-    if (col < SYM_N) part[(size_t)blockIdx.x * SYM_N + col] = m;
+    if (col < sn) part[(size_t)blockIdx.x * sn + col] = m;
 }
 
-__global__ void sym_colscale_kernel(const float *part, int nb, float *scale, float *colinv) {
+__global__ void sym_colscale_kernel(const float *part, int nb, int sn, float *scale, float *colinv) {
     const int col = threadIdx.x;
-    if (col >= SYM_N) return;
+    if (col >= sn) return;
     float m = 0.f;
-    for (int b = 0; b < nb; ++b) m = fmaxf(m, part[(size_t)b * SYM_N + col]);
+    for (int b = 0; b < nb; ++b) m = fmaxf(m, part[(size_t)b * sn + col]);
     int e = 0;
     if (m > 0.f) frexpf(m, &e);
     const float s = ldexpf(1.0f, -e);
@@ -512,57 +535,65 @@ __global__ void sym_colscale_kernel(const float *part, int nb, float *scale, flo
     colinv[col] = 1.0f / s;
 }
 
-int sym_stages(int d, int nprod, int c) {
-    for (int s = 4; s >= 2; --s)
-        if (make_sym_layout(d, nprod, c, s).total <= 225 * 1024) return s;
-    return 0;
-}
-
-template <int KIND, int DC, int NPROD, bool BF16>
+template <int KIND, int DC, int NPROD, bool BF16, int SN>
 int launch_sym(const SymParams &p, const SymLayout &L, cudaStream_t st) {
-    auto fn = kz_sym_kernel<KIND, DC, NPROD, BF16>;
+    auto fn = kz_sym_kernel<KIND, DC, NPROD, BF16, SN>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) {
         set_error("kz_sym: cannot reserve %d bytes of shared memory: %s", L.total, cudaGetErrorString(e));
         return LD_ERR_CUDA;
     }
     const double nn = (double)p.n * (double)p.n;
-    const int slot = prof_begin_launch(st, nn, 2.0 * nn * SYM_N * NPROD);
+    const int slot = prof_begin_launch(st, nn, 2.0 * nn * SN * NPROD);
     fn<<<p.NB, SNTHREADS, L.total, st>>>(p, L);
     prof_end_launch(st, slot);
     return check_launch("kz_sym_kernel");
 }
 
-template <int KIND, int NPROD, bool BF16>
+template <int KIND, int NPROD, bool BF16, int SN>
 int launch_sym_d(const SymParams &p, const SymLayout &L, cudaStream_t st) {
     switch (p.d) {
-        case 1: return launch_sym<KIND, 1, NPROD, BF16>(p, L, st);
-        case 2: return launch_sym<KIND, 2, NPROD, BF16>(p, L, st);
-        case 3: return launch_sym<KIND, 3, NPROD, BF16>(p, L, st);
-        case 4: return launch_sym<KIND, 4, NPROD, BF16>(p, L, st);
-        default: return launch_sym<KIND, 0, NPROD, BF16>(p, L, st);
+        case 1: return launch_sym<KIND, 1, NPROD, BF16, SN>(p, L, st);
+        case 2: return launch_sym<KIND, 2, NPROD, BF16, SN>(p, L, st);
+        case 3: return launch_sym<KIND, 3, NPROD, BF16, SN>(p, L, st);
+        case 4: return launch_sym<KIND, 4, NPROD, BF16, SN>(p, L, st);
+        default: return launch_sym<KIND, 0, NPROD, BF16, SN>(p, L, st);
     }
 }
+
+template <int SN>
+int launch_sym_all(int kind, int nprod, bool bf16, const SymParams &p, const SymLayout &L, cudaStream_t st) {
+    if (kind == LD_RBF) {
+        if (bf16) return launch_sym_d<LD_RBF, 1, true, SN>(p, L, st);
+        if (nprod == 3) return launch_sym_d<LD_RBF, 3, false, SN>(p, L, st);
+        return launch_sym_d<LD_RBF, 1, false, SN>(p, L, st);
+    }
+    if (bf16) return launch_sym_d<LD_MATERN52, 1, true, SN>(p, L, st);
+    if (nprod == 3) return launch_sym_d<LD_MATERN52, 3, false, SN>(p, L, st);
+    return launch_sym_d<LD_MATERN52, 1, false, SN>(p, L, st);
+}
+
+int sym_width(int c) { return c <= 16 ? 16 : SN_MAX; }
 
 }  // namespace
 
 bool kz_sym_eligible(int64_t n, int d, int c, int precision) {
     const int nprod = precision == LD_F16X3_TC ? 3 : 1;
-    return c <= SYM_N && n >= 2 * BR && d <= 8 && sym_stages(d, nprod, c) > 0;
+    return c <= SN_MAX && n >= 2 * BR && d <= 8 && sym_stages(sym_width(c), d, nprod) > 0;
 }
 
 size_t kz_sym_workspace(int64_t n, int d, int c, int precision) {
     const int64_t NB = (n + BR - 1) / BR;
     const int nprod = precision == LD_F16X3_TC ? 3 : 1;
+    const int sn = sym_width(c);
     Arena a;
     a.measuring = true;
     a.take<float>((size_t)NB * BR * d);
-    a.take<uint8_t>((size_t)NB * (nprod == 3 ? 2 : 1) * SYM_N * BR * 2);
-    a.take<float>(SYM_N);
-    a.take<float>(SYM_N);
-    a.take<float>((size_t)256 * SYM_N);
+    a.take<uint8_t>((size_t)NB * (nprod == 3 ? 2 : 1) * sn * BR * 2);
+    a.take<float>(sn);
+    a.take<float>(sn);
+    a.take<float>((size_t)256 * sn);
     a.take<int>(4);
-    (void)c;
     return a.off;
 }
 
@@ -571,12 +602,13 @@ int kz_sym(const float *Xs, int64_t n, int d, int kind, double variance, double 
     const int64_t NB = (n + BR - 1) / BR;
     const int nprod = precision == LD_F16X3_TC ? 3 : 1;
     const bool bf16 = precision == LD_BF16_TC;
+    const int sn = sym_width(c);
     const size_t mark = ws.off;
     float *Xp = ws.take<float>((size_t)NB * BR * d);
-    uint8_t *img = ws.take<uint8_t>((size_t)NB * (nprod == 3 ? 2 : 1) * SYM_N * BR * 2);
-    float *scale = ws.take<float>(SYM_N);
-    float *colinv = ws.take<float>(SYM_N);
-    float *part = ws.take<float>((size_t)256 * SYM_N);
+    uint8_t *img = ws.take<uint8_t>((size_t)NB * (nprod == 3 ? 2 : 1) * sn * BR * 2);
+    float *scale = ws.take<float>(sn);
+    float *colinv = ws.take<float>(sn);
+    float *part = ws.take<float>((size_t)256 * sn);
     int *err = ws.take<int>(4);
     if (ws.overflow || !Xp) {
         set_error("kz_sym: workspace too small");
@@ -587,13 +619,13 @@ int kz_sym(const float *Xs, int64_t n, int d, int kind, double variance, double 
         const float factor = kind == LD_RBF ? 1.2011224087864498f : 1.4426950408889634f;
         const int64_t cnt = NB * BR * d;
         sym_point_tiles_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(Xs, n, d, factor, NB, Xp);
-        sym_colmax_kernel<<<256, 32, 0, st>>>(V, n, c, part);
-        sym_colscale_kernel<<<1, 32, 0, st>>>(part, 256, scale, colinv);
-        const int64_t nthr = NB * SYM_N * (BR / 8);
+        sym_colmax_kernel<<<256, 64, 0, st>>>(V, n, c, sn, part);
+        sym_colscale_kernel<<<1, 64, 0, st>>>(part, 256, sn, scale, colinv);
+        const int64_t nthr = NB * sn * (BR / 8);
         const unsigned gb = (unsigned)((nthr + 255) / 256);
-        if (bf16) sym_image_kernel<true, 1><<<gb, 256, 0, st>>>(V, n, c, (int)NB, scale, img);
-        else if (nprod == 3) sym_image_kernel<false, 3><<<gb, 256, 0, st>>>(V, n, c, (int)NB, scale, img);
-        else sym_image_kernel<false, 1><<<gb, 256, 0, st>>>(V, n, c, (int)NB, scale, img);
+        if (bf16) sym_image_kernel<true, 1><<<gb, 256, 0, st>>>(V, n, c, sn, (int)NB, scale, img);
+        else if (nprod == 3) sym_image_kernel<false, 3><<<gb, 256, 0, st>>>(V, n, c, sn, (int)NB, scale, img);
+        else sym_image_kernel<false, 1><<<gb, 256, 0, st>>>(V, n, c, sn, (int)NB, scale, img);
         LD_TRY(check_launch("kz_sym prep", 4));
         LD_CHECK_CUDA(cudaMemsetAsync(W, 0, sizeof(float) * (size_t)n * c, st));
         LD_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
@@ -607,22 +639,16 @@ int kz_sym(const float *Xs, int64_t n, int d, int kind, double variance, double 
         p.d = d;
         p.c = c;
         p.NB = (int)NB;
-        const int tcols = (nprod == 3 ? 4 : 3) * SYM_N;  // D (x2 when drained) + two D'
-        p.ncols_tmem = tcols <= 32 ? 32 : (tcols <= 64 ? 64 : 128);
-        p.bulk_ok = (reinterpret_cast<uintptr_t>(W) % 16 == 0) && ((c * 4) % 16 == 0);
+        // D (x2 when drained, 2 SN wide with the hi/lo split) + two D'
+        const int tcols = nprod == 3 ? 8 * sn : 3 * sn;
+        p.ncols_tmem = tcols <= 32 ? 32 : (tcols <= 64 ? 64 : (tcols <= 128 ? 128 : (tcols <= 256 ? 256 : 512)));
+        p.vec_ok = (reinterpret_cast<uintptr_t>(W) % 16 == 0) && ((c * 4) % 16 == 0);
         p.variance = (float)variance;
         p.noise = (float)noise;
         p.err = err;
-        const SymLayout L = make_sym_layout(d, nprod, c, sym_stages(d, nprod, c));
-        if (kind == LD_RBF) {
-            if (bf16) LD_TRY(launch_sym_d<LD_RBF, 1, true>(p, L, st));
-            else if (nprod == 3) LD_TRY(launch_sym_d<LD_RBF, 3, false>(p, L, st));
-            else LD_TRY(launch_sym_d<LD_RBF, 1, false>(p, L, st));
-        } else {
-            if (bf16) LD_TRY(launch_sym_d<LD_MATERN52, 1, true>(p, L, st));
-            else if (nprod == 3) LD_TRY(launch_sym_d<LD_MATERN52, 3, false>(p, L, st));
-            else LD_TRY(launch_sym_d<LD_MATERN52, 1, false>(p, L, st));
-        }
+        const SymLayout L = make_sym_layout(sn, d, nprod, sym_stages(sn, d, nprod));
+        if (sn == 16) LD_TRY(launch_sym_all<16>(kind, nprod, bf16, p, L, st));
+        else LD_TRY(launch_sym_all<SN_MAX>(kind, nprod, bf16, p, L, st));
         int herr = 0;
         LD_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
         LD_CHECK_CUDA(cudaStreamSynchronize(st));

@@ -38,14 +38,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// try_wait with a suspend-time hint (ns): while the phase is incomplete the thread
+// is parked until the phase completes or the hint runs out, instead of spinning
+// and taking issue slots from the warps that compute.
+constexpr uint32_t SUSPEND_HINT_NS = 1000000;
+__device__ __forceinline__ bool mbar_try_wait_parked(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(SUSPEND_HINT_NS)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait (budget in SM cycles); false on timeout.
+__device__ __forceinline__ bool mbar_wait_budget(uint64_t *bar, uint32_t parity, long long budget) {
     if (mbar_try_wait(bar, parity)) return true;
     long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > WAIT_BUDGET) return false;
+    while (!mbar_try_wait_parked(bar, parity)) {
+        if (clock64() - t0 > budget) return false;
     }
     return true;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    return mbar_wait_budget(bar, parity, WAIT_BUDGET);
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(

@@ -116,13 +116,15 @@ def test_kz_bench_workload_sampled_rows():
     assert relerr(W[rows], ref) < 2 * np.sqrt(n) * 2.0 ** -24 + 2.0 ** -19
 
 
-# The symmetric product (c <= 16): one CTA per 128-row block visits half of the
-# blocks, so cover NB = 2 (even, tie rule), odd NB, a ragged last block, 1..16
-# columns, c * 4 not a multiple of 16 (per-element adds instead of bulk adds)
-# and a dimension above 4 (the generic-d instance).
+# The symmetric product (c <= 48; compiled for 16 and 48 columns): one CTA per
+# 128-row block visits half of the blocks, so cover NB = 2 (even, tie rule), odd
+# NB, a ragged last block, 1..48 columns on both widths, c * 4 not a multiple of 16
+# (per-element adds instead of vector adds) and a dimension above 4 (the generic-d
+# instance).
 @pytest.mark.parametrize("prec", ["f16x3_tc", "f16_tc", "bf16_tc"])
 @pytest.mark.parametrize("kind", [api.RBF, api.MATERN52])
-@pytest.mark.parametrize("n,d,c", [(256, 2, 16), (257, 3, 7), (384, 4, 1), (4133, 4, 16), (1536, 1, 12), (700, 6, 9)])
+@pytest.mark.parametrize("n,d,c", [(256, 2, 16), (257, 3, 7), (384, 4, 1), (4133, 4, 16), (1536, 1, 12), (700, 6, 9),
+                                   (1000, 2, 48), (513, 3, 33), (4133, 4, 17), (2560, 4, 40)])
 def test_kz_symmetric_tensor_core_matches_oracle(prec, kind, n, d, c):
     X = inputs.points(n, d, "uniform", seed=31)
     V = inputs.gaussian(n, c, seed=32)
