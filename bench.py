@@ -263,9 +263,11 @@ def run_ours(args, rank, world, local_rank, pool):
                 seed=rank_probe_seed(rank))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    def step(Xd):
+    def step(Xd, mid=None):
         P = api.Precond.build(Xd, kern, w["rank"], power_iters=w["power_iters"],
                               seed=inputs.SEED_SKETCH, precision=args.sketch_precision)
+        if mid is not None:
+            mid.record(torch.cuda.current_stream())  # preconditioner built
         res = api.logdet_estimate(Xd, kern, precond=P, **opts)
         P.free()
         return res
@@ -289,20 +291,27 @@ def run_ours(args, rank, world, local_rank, pool):
     launches0 = lib.ld_launch_count()
     lib.ld_profile_begin()
     results = []
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for k in range(args.steps):
         flush.fill_(k & 0xFF)
         ev[k][0].record(stream)
-        results.append(step(X))
+        results.append(step(X, mids[k]))
         ev[k][1].record(stream)
     import ctypes
     kz_ms, kz_n, kz_pairs, kz_flops = (ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(),
                                       ctypes.c_double())
     lib.ld_profile_end(ctypes.byref(kz_ms), ctypes.byref(kz_n), ctypes.byref(kz_pairs), ctypes.byref(kz_flops))
+    per_kernel = {}
+    for kid, kname_ in ((1, "kz_sym_kernel"), (0, "kz_tc_kernel")):
+        m_, n_, p_, f_ = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        lib.ld_profile_kernel(kid, ctypes.byref(m_), ctypes.byref(n_), ctypes.byref(p_), ctypes.byref(f_))
+        per_kernel[kname_] = (m_.value, n_.value, p_.value, f_.value)
     torch.cuda.synchronize()
     barrier()
     launches = lib.ld_launch_count() - launches0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    build_ms = [ev[k][0].elapsed_time(mids[k]) for k in range(args.steps)]
     total_ms = sum(step_ms)
     total_ms_max = max_over_ranks(total_ms, world, dev)
     value = job_value(world, args.steps, total_ms_max)
@@ -329,11 +338,30 @@ def run_ours(args, rank, world, local_rank, pool):
     if rank != 0:
         return None
 
-    avg_launch_ms = kz_ms.value / max(1, kz_n.value)
-    pairs_per_launch = kz_pairs.value / max(1, kz_n.value)
-    achieved = pairs_per_launch / (avg_launch_ms / 1e3) / 1e9  # Gpair/s
     kname = "matern52" if w["kind"] == inputs.MATERN52 else "rbf"
     peak = pair_peak_gps(kname, d)
+    tc_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops") \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+
+    def roof(name):
+        """ALU roofline of one kernel over the timed region: distinct kernel evaluations
+        per launch over the launch's average CUDA-event time."""
+        ms, nl, pairs, flops = per_kernel[name]
+        if nl == 0:
+            return None
+        avg = ms / nl
+        ach = pairs / nl / (avg / 1e3) / 1e9
+        out = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gpair/s",
+               "frac": ach / peak, "traffic": None, "launches": nl, "avg_launch_ms": avg,
+               "share_of_step": ms / total_ms, "tensor_tflops": flops / (ms / 1e3) / 1e12,
+               "peak_note": "ALU roofline of the pair evaluation derived from measured GB300 pipe rates"}
+        if tc_peak:
+            out["tensor_frac_of_measured_bf16"] = out["tensor_tflops"] / tc_peak
+        return out
+
+    sym_roof, tc_roof = roof("kz_sym_kernel"), roof("kz_tc_kernel")
+    dominant, other = (sym_roof, tc_roof) if (sym_roof and (not tc_roof or per_kernel["kz_sym_kernel"][0] >=
+                                                            per_kernel["kz_tc_kernel"][0])) else (tc_roof, sym_roof)
     res = results[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -347,13 +375,17 @@ def run_ours(args, rank, world, local_rank, pool):
                    "l2": "flushed between steps (256 MiB write, outside step events)"},
         "probe_matvecs_per_s": world * args.steps * (w["probes"] * args.t + w["probes"] * w["order"])
                                / (total_ms_max / 1e3),
+        "sketch_matvecs_per_s": world * args.steps * (w["power_iters"] + 2) * w["rank"] / (total_ms_max / 1e3),
+        "precond_build_ms": statistics.mean(build_ms),
+        "estimates_per_s_precond_amortised": 1e3 / statistics.mean(
+            [s_ - b_ for s_, b_ in zip(step_ms, build_ms)]) * world,
         "estimate": {"logdet": res["logdet"], "logdet_P": res["logdet_P"], "std_err": res["std_err"],
                      "iters": res["iters"], "max_resid": res["max_resid"][:w["order"]]},
-        "roofline": {"kernel": "kz_tc_kernel", "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
-                     "launches": kz_n.value, "avg_launch_ms": avg_launch_ms,
-                     "share_of_step": kz_ms.value / total_ms,
-                     "tensor_tflops": kz_flops.value / (kz_ms.value / 1e3) / 1e12},
+        "roofline": dominant,
+        "roofline_other_kernel": other,
+        "kernel_products": {"launches": kz_n.value, "device_ms": kz_ms.value, "share_of_step": kz_ms.value / total_ms,
+                            "product_pairs_per_s": (per_kernel["kz_sym_kernel"][1] + per_kernel["kz_tc_kernel"][1])
+                            * float(n) * n / (kz_ms.value / 1e3) if kz_ms.value else None},
         "clocks": clk,
         "gpu_launches": int(launches),
         "e2e": e2e,

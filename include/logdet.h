@@ -266,7 +266,8 @@ int logdet_grad(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
  * ld_profile_begin / ld_profile_end: between the two calls every launch of the
  * kernel product (the O(n^2) step) is bracketed by CUDA events recorded on its
  * own stream; end synchronises those events and returns the summed device
- * time (ms), the launch count, the kernel evaluations (n^2 per launch) and the
+ * time (ms), the launch count, the kernel evaluations (n^2 per launch; n(n+1)/2
+ * for the symmetric product, which evaluates each pair once) and the
  * multiply-add flops (2 n^2 c per product) they did.  Single-threaded use. */
 int64_t ld_launch_count(void);
 /* Failure-detection self-test: one thread waits on an mbarrier that nothing
@@ -276,6 +277,10 @@ int64_t ld_launch_count(void);
 int ld_selftest_wait_timeout(int64_t budget_cycles, void *stream);
 int ld_profile_begin(void);
 int ld_profile_end(double *kz_ms, int64_t *kz_launches, double *kz_pairs, double *kz_mma_flops);
+/* The same totals of the last closed window for one kernel: 0 the general
+ * tensor-core product, 1 the symmetric tensor-core product, 2 the SIMT product,
+ * 3 the stored dense product.  LD_ERR_INVALID for another id. */
+int ld_profile_kernel(int32_t kernel, double *ms, int64_t *launches, double *pairs, double *mma_flops);
 
 /* --------------------------------------------------------------- surrogate
  * MLP 4 -> 128 -> 128 -> 128 -> 1 with exact GELU, fp32, trained by Adam on

@@ -92,6 +92,7 @@ _SIGS = {
     "ld_selftest_wait_timeout": (c_int32, [c_int64, _P]),
     "ld_profile_begin": (c_int32, []),
     "ld_profile_end": (c_int32, [_P, _P, _P, _P]),
+    "ld_profile_kernel": (c_int32, [c_int32, _P, _P, _P, _P]),
     "surrogate_create": (c_int32, [c_uint64, _P, _P]),
     "surrogate_set_params": (c_int32, [_P, _P, _P]),
     "surrogate_get_params": (c_int32, [_P, _P, _P]),

@@ -67,7 +67,7 @@ int dense_materialize(const T *Xs, int64_t n, int d, const ld_kernel &k, T *M, c
 template <typename T>
 int dense_product(const T *M, int64_t n, const T *V, T *W, int c, cudaStream_t st) {
     const double nn = (double)n * (double)n;
-    const int slot = prof_begin_launch(st, nn, 2.0 * nn * c);
+    const int slot = prof_begin_launch(st, PROF_DENSE, nn, 2.0 * nn * c);
     int code = gemm_nn<T>(n, c, (int)n, T(1), M, n, V, c, T(0), W, c, st);
     prof_end_launch(st, slot);
     return code;

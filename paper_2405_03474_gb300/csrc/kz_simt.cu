@@ -99,7 +99,7 @@ int launch_kz(const T *Xs, int64_t n, int d, const T *V, T *W, T *Wdl, int c, T 
               T inv_l, cudaStream_t st) {
     dim3 grid((unsigned)((n + TPB - 1) / TPB), (unsigned)((c + CC - 1) / CC));
     const double nn = (double)n * (double)n;
-    const int slot = prof_begin_launch(st, nn, 2.0 * nn * c * (DERIV ? 2 : 1));
+    const int slot = prof_begin_launch(st, PROF_KZ_SIMT, nn, 2.0 * nn * c * (DERIV ? 2 : 1));
     switch (d) {
         case 1: kz_simt_kernel<T, KIND, 1, DERIV><<<grid, TPB, 0, st>>>(Xs, n, d, V, W, Wdl, c, var, noise, inv_l); break;
         case 2: kz_simt_kernel<T, KIND, 2, DERIV><<<grid, TPB, 0, st>>>(Xs, n, d, V, W, Wdl, c, var, noise, inv_l); break;

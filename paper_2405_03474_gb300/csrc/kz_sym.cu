@@ -543,8 +543,9 @@ int launch_sym(const SymParams &p, const SymLayout &L, cudaStream_t st) {
         set_error("kz_sym: cannot reserve %d bytes of shared memory: %s", L.total, cudaGetErrorString(e));
         return LD_ERR_CUDA;
     }
+    // distinct kernel values evaluated: n (n + 1) / 2; tensor flops: D and D' per block
     const double nn = (double)p.n * (double)p.n;
-    const int slot = prof_begin_launch(st, nn, 2.0 * nn * SN * NPROD);
+    const int slot = prof_begin_launch(st, PROF_KZ_SYM, 0.5 * ((double)p.n * (double)(p.n + 1)), 2.0 * nn * SN * NPROD);
     fn<<<p.NB, SNTHREADS, L.total, st>>>(p, L);
     prof_end_launch(st, slot);
     return check_launch("kz_sym_kernel");

@@ -467,7 +467,7 @@ int launch_main(const TcParams &p, const Layout &L, int nblocks, cudaStream_t st
         return LD_ERR_CUDA;
     }
     const double nn = (double)p.n * (double)p.n;
-    const int slot = prof_begin_launch(st, nn, 2.0 * nn * p.N * NPROD);
+    const int slot = prof_begin_launch(st, PROF_KZ_TC, nn, 2.0 * nn * p.N * NPROD);
     fn<<<nblocks, NTHREADS, L.total, st>>>(p, L);
     prof_end_launch(st, slot);
     return check_launch("kz_tc_kernel");

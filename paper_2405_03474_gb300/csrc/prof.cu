@@ -11,19 +11,26 @@ std::atomic<long long> g_launches{0};
 struct Rec {
     cudaEvent_t a = nullptr, b = nullptr;
     double pairs = 0, flops = 0;
+    int kernel = 0;
+};
+struct Total {
+    double ms = 0, pairs = 0, flops = 0;
+    int64_t launches = 0;
 };
 bool g_on = false;
 std::vector<Rec> g_recs;
+Total g_last[PROF_KERNELS];  // per kernel, of the last closed profile window
 }  // namespace
 
 void count_launches(int k) { g_launches += k; }
 
-int prof_begin_launch(cudaStream_t st, double pairs, double mma_flops) {
+int prof_begin_launch(cudaStream_t st, int kernel, double pairs, double mma_flops) {
     if (!g_on) return -1;
     Rec r;
     if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
     r.pairs = pairs;
     r.flops = mma_flops;
+    r.kernel = kernel >= 0 && kernel < PROF_KERNELS ? kernel : 0;
     cudaEventRecord(r.a, st);
     g_recs.push_back(r);
     return (int)g_recs.size() - 1;
@@ -56,6 +63,7 @@ int ld_profile_end(double *kz_ms, int64_t *kz_launches, double *kz_pairs, double
     ld::g_on = false;
     double ms = 0, pairs = 0, flops = 0;
     int code = LD_OK;
+    for (auto &t : ld::g_last) t = ld::Total();
     for (auto &r : ld::g_recs) {
         float t = 0.f;
         if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {
@@ -65,6 +73,11 @@ int ld_profile_end(double *kz_ms, int64_t *kz_launches, double *kz_pairs, double
         ms += t;
         pairs += r.pairs;
         flops += r.flops;
+        ld::Total &k = ld::g_last[r.kernel];
+        k.ms += t;
+        k.pairs += r.pairs;
+        k.flops += r.flops;
+        k.launches += 1;
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
@@ -74,6 +87,20 @@ int ld_profile_end(double *kz_ms, int64_t *kz_launches, double *kz_pairs, double
     if (kz_mma_flops) *kz_mma_flops = flops;
     ld::g_recs.clear();
     return code;
+}
+
+int ld_profile_kernel(int32_t kernel, double *ms, int64_t *launches, double *pairs, double *mma_flops) {
+    ld::clear_error();
+    if (kernel < 0 || kernel >= ld::PROF_KERNELS) {
+        ld::set_error("ld_profile_kernel: kernel id %d out of range", kernel);
+        return LD_ERR_INVALID;
+    }
+    const ld::Total &k = ld::g_last[kernel];
+    if (ms) *ms = k.ms;
+    if (launches) *launches = k.launches;
+    if (pairs) *pairs = k.pairs;
+    if (mma_flops) *mma_flops = k.flops;
+    return LD_OK;
 }
 
 }  // extern "C"
