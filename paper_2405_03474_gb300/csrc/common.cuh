@@ -128,6 +128,11 @@ int dense_product(const T *M, int64_t n, const T *V, T *W, int c, cudaStream_t s
 // tensor-core product (float vectors)
 size_t kz_tc_workspace(int64_t n, int d, int c, int precision);
 // symmetric tensor-core product for c <= 16 (each kernel value evaluated once)
+// the one-pass product for 256 < c <= 512 columns, single fp16 / bf16 product (kz_wide.cu)
+bool kz_wide_eligible(int64_t n, int d, int c, int precision);
+size_t kz_wide_workspace(int64_t n, int d, int c, int precision);
+int kz_wide(const float *Xs, int64_t n, int d, int kind, double variance, double noise, const float *V,
+            float *W, int c, int precision, Arena &ws, cudaStream_t st);
 bool kz_sym_eligible(int64_t n, int d, int c, int precision);
 size_t kz_sym_workspace(int64_t n, int d, int c, int precision);
 int kz_sym(const float *Xs, int64_t n, int d, int kind, double variance, double noise, const float *V, float *W,

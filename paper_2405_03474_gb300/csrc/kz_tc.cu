@@ -498,6 +498,7 @@ int launch_d(const TcParams &p, const Layout &L, int nblocks, cudaStream_t st) {
 
 size_t kz_tc_workspace(int64_t n, int d, int c, int precision) {
     if (kz_sym_eligible(n, d, c, precision)) return kz_sym_workspace(n, d, c, precision);
+    if (kz_wide_eligible(n, d, c, precision)) return kz_wide_workspace(n, d, c, precision);
     const int64_t ntiles = (n + TJ - 1) / TJ;
     const int N = chunk_N(c);
     const int nprod = nprod_of(precision);
@@ -521,6 +522,8 @@ int kz_tc(const float *Xs, int64_t n, int d, int kind, double variance, double n
     }
     if (kz_sym_eligible(n, d, c, precision))
         return kz_sym(Xs, n, d, kind, variance, noise, V, W, c, precision, ws, st);
+    if (kz_wide_eligible(n, d, c, precision))
+        return kz_wide(Xs, n, d, kind, variance, noise, V, W, c, precision, ws, st);
     const int64_t ntiles = (n + TJ - 1) / TJ;
     const int nprod = nprod_of(precision);
     const bool bf16 = precision == LD_BF16_TC;

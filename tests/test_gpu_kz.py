@@ -80,14 +80,29 @@ TC_TOL = {"f16_tc": 2.0 ** -9, "bf16_tc": 2.0 ** -6, "f16x3_tc": 2.0 ** -16}
 
 @pytest.mark.parametrize("prec", ["f16x3_tc", "f16_tc", "bf16_tc"])
 @pytest.mark.parametrize("kind", [api.RBF, api.MATERN52])
-@pytest.mark.parametrize("n,d,c", [(1000, 2, 16), (777, 4, 48), (300, 3, 5), (2000, 4, 256), (640, 1, 300)])
+@pytest.mark.parametrize("n,d,c", [(1000, 2, 16), (777, 4, 48), (300, 3, 5), (2000, 4, 256), (640, 1, 300),
+                                   (1000, 4, 512), (700, 3, 264)])
 def test_kz_tensor_core_matches_oracle(prec, kind, n, d, c):
+    # (256 < c <= 512 in fp16 / bf16 runs the one-pass wide kernel; hi/lo fp16 above 48 columns
+    # the general kernel in 256-column chunks)
     X = inputs.points(n, d, "uniform", seed=11)
     V = inputs.gaussian(n, c, seed=12)
     k = api.Kernel(kind, 0.15, 1.7, 1e-2)
     W = host(api.ld_kz(cuda(X), cuda(V, torch.float32), k, prec))
     ref = kernels.kernel_matrix(X, kind, 0.15, 1.7, 1e-2) @ V
     assert relerr(W, ref) < TC_TOL[prec]
+
+
+def test_kz_wide_sketch_sampled_rows_at_large_n():
+    # the sketch product as the preconditioner build calls it: 512 columns, fp16, n = 2^18
+    n, d, c = 1 << 18, 4, 512
+    X = inputs.points(n, d, "uniform", seed=0)
+    V = inputs.gaussian(n, c, seed=8)
+    k = api.Kernel(api.MATERN52, 0.1, 1.0, 1e-2)
+    W = host(api.ld_kz(cuda(X), cuda(V, torch.float32), k, "f16_tc"))
+    rows = np.concatenate([np.random.default_rng(2).choice(n, 12, replace=False), [0, n - 1]])
+    ref = kernels.kz_rows(X, V, rows, api.MATERN52, 0.1, 1.0, 1e-2)
+    assert relerr(W[rows], ref) < TC_TOL["f16_tc"]
 
 
 def test_kz_f16x3_sampled_rows_at_large_n():
