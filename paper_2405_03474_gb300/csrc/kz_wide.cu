@@ -6,9 +6,11 @@
 // Here one CTA per SM owns all 512 TMEM columns: the 128 x 64 tile K_IJ is
 // evaluated once by 16 eval warps (2 rows x 8 j per thread, packed f32x2, MUFU
 // sqrt + ex2) and multiplied into both 256-column halves of D by two tcgen05.mma
-// per K-step; the operand image of V streams through two 64 KB stages (the CTAs of
-// one wave walk the j-tiles in the same order, so each tile is read from L2 by all
-// of them).  D accumulates over all j-tiles in tensor memory (fp32, no drains: the
+// per K-step; the operand image of V streams through a ring of half-tile stages
+// (one 256-column half, 32 KB, per stage, each with its own barrier, so several
+// loads are in flight and each half's MMAs start when it lands; the CTAs of one
+// wave walk the j-tiles in the same order, so each tile is read from L2 by all of
+// them).  D accumulates over all j-tiles in tensor memory (fp32, no drains: the
 // single-product forms are for the sketch, whose accuracy is set by fp16 rounding
 // of K and V) and is written once at the end.  Every mbarrier wait is bounded.
 #include <math.h>
@@ -32,6 +34,9 @@ constexpr int WA_BYTES = WM * WJ * 2;   // one 128 x 64 tile of halves
 constexpr int WSBO = (WJ / 8) * 128;    // 1024: byte step between 8-row groups
 constexpr int W_MAXN = 512;
 constexpr int W_HALF = 256;             // MMA N of the first half
+constexpr int WSA = 4;                  // K-tile stages (evaluation runs up to 4 tiles ahead of the MMA)
+constexpr int WXS = 8;                  // point-coordinate stages (their own ring, so the evaluation
+                                        // does not wait for the operand image)
 
 struct WideParams {
     const float *Xp;     // per 64-point tile: d x 64 floats, far-padded, log2 e folded in
@@ -45,18 +50,23 @@ struct WideParams {
     int *err;
 };
 
+// Ring of SL half-tile stages: stage m % SL holds half h = m % 2 of j-tile m / 2
+// (h0_bytes = 256 columns, h1_bytes = N - 256); the point coordinates of the
+// j-tiles (x_bytes each) have a ring of WXS stages of their own.
 struct WideLayout {
-    int sl, b_bytes, x_bytes, l_bytes, a_off, l_off, total;
+    int sl, h0_bytes, h1_bytes, x_bytes, l_bytes, a_off, x_off, l_off, total;
 };
 
 WideLayout make_wide_layout(int N, int d, int sl) {
     WideLayout L;
     L.sl = sl;
-    L.b_bytes = N * WJ * 2;
+    L.h0_bytes = W_HALF * WJ * 2;
+    L.h1_bytes = (N - W_HALF) * WJ * 2;
     L.x_bytes = WJ * d * 4;
-    L.l_bytes = ((L.b_bytes + L.x_bytes + 1023) / 1024) * 1024;
+    L.l_bytes = L.h0_bytes;
     L.a_off = 1024;
-    L.l_off = L.a_off + 2 * WA_BYTES;
+    L.x_off = L.a_off + WSA * WA_BYTES;
+    L.l_off = L.x_off + ((WXS * L.x_bytes + 1023) / 1024) * 1024;
     L.total = L.l_off + sl * L.l_bytes + 1024;
     return L;
 }
@@ -66,14 +76,17 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);  // [sl]
-    uint64_t *empty = full + 4;                           // [sl]
-    uint64_t *afull = empty + 4;                          // [2]
-    uint64_t *aempty = afull + 2;                         // [2]
-    uint64_t *done = aempty + 2;
+    uint64_t *empty = full + 8;                           // [sl]
+    uint64_t *afull = empty + 8;                          // [WSA]
+    uint64_t *aempty = afull + WSA;                       // [WSA]
+    uint64_t *xfull = aempty + WSA;                       // [WXS]
+    uint64_t *xempty = xfull + WXS;                       // [WXS]
+    uint64_t *done = xempty + WXS;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     int *s_err = reinterpret_cast<int *>(tmem_slot + 1);
     uint8_t *abase = smem + L.a_off;
     uint8_t *lbase = smem + L.l_off;
+    uint8_t *xbase = smem + L.x_off;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -87,9 +100,13 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < WSA; ++s) {
             mbar_init(&afull[s], WEVAL * 32);
             mbar_init(&aempty[s], 1);
+        }
+        for (int s = 0; s < WXS; ++s) {
+            mbar_init(&xfull[s], 1);
+            mbar_init(&xempty[s], WEVAL * 32);
         }
         mbar_init(done, 1);
         *s_err = 0;
@@ -110,22 +127,37 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
     if (warp == WEVAL + 1) {
         // ---------------- producer: operand image and point tile of each j-tile
         if (lane == 0) {
-            const uint32_t xb = (uint32_t)(WJ * dd * 4);
-            const uint32_t bb = (uint32_t)L.b_bytes;
-            int t = 0;
-            for (; t < T; ++t) {
-                const int s = t % SL;
-                if (t >= SL && !mbar_wait(&empty[s], ((t / SL) - 1) & 1)) {
+            const size_t tile_bytes = (size_t)L.h0_bytes + L.h1_bytes;
+            const int M = 2 * T;  // half-tile loads
+            int m = 0;
+            for (; m < M; ++m) {
+                const int s = m % SL, t = m >> 1, h = m & 1;
+                if (m >= SL && !mbar_wait(&empty[s], ((m / SL) - 1) & 1)) {
                     atomicOr(s_err, ERR_TIMEOUT);
                     break;
                 }
                 uint8_t *st = lbase + (size_t)s * L.l_bytes;
-                mbar_expect_tx(&full[s], xb + bb);
-                bulk_g2s(st, p.img + (size_t)t * bb, bb, &full[s]);
-                bulk_g2s(st + L.b_bytes, p.Xp + (size_t)t * WJ * dd, xb, &full[s]);
+                const uint32_t hb = (uint32_t)(h ? L.h1_bytes : L.h0_bytes);
+                mbar_expect_tx(&full[s], hb);
+                bulk_g2s(st, p.img + (size_t)t * tile_bytes + (h ? (size_t)L.h0_bytes : 0), hb, &full[s]);
             }
-            for (int u = std::max(0, t - SL); u < t; ++u)
+            for (int u = std::max(0, m - SL); u < m; ++u)
                 if (!mbar_wait(&full[u % SL], (u / SL) & 1)) atomicOr(s_err, ERR_TIMEOUT);
+        } else if (lane == 1) {
+            // point coordinates of each j-tile, ahead of the evaluation
+            const uint32_t xb = (uint32_t)L.x_bytes;
+            int t = 0;
+            for (; t < T; ++t) {
+                const int s = t % WXS;
+                if (t >= WXS && !mbar_wait(&xempty[s], ((t / WXS) - 1) & 1)) {
+                    atomicOr(s_err, ERR_TIMEOUT);
+                    break;
+                }
+                mbar_expect_tx(&xfull[s], xb);
+                bulk_g2s(xbase + (size_t)s * xb, p.Xp + (size_t)t * WJ * dd, xb, &xfull[s]);
+            }
+            for (int u = std::max(0, t - WXS); u < t; ++u)
+                if (!mbar_wait(&xfull[u % WXS], (u / WXS) & 1)) atomicOr(s_err, ERR_TIMEOUT);
         }
     } else if (warp == WEVAL) {
         // ---------------- MMA issuer: D[:, 0:256] and D[:, 256:N] += K_IJ V_J
@@ -133,24 +165,30 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
             const uint32_t idesc0 = make_idesc(WM, W_HALF, BF16 ? 1u : 0u);
             const uint32_t idesc1 = make_idesc(WM, p.N - W_HALF, BF16 ? 1u : 0u);
             bool ok = true;
-            for (int t = 0; t < T; ++t) {
-                const int s = t % SL, sa = t & 1;
-                if (!mbar_wait(&afull[sa], (t >> 1) & 1) || !mbar_wait(&full[s], (t / SL) & 1)) {
+            for (int t = 0; t < T && ok; ++t) {
+                const int sa = t % WSA;
+                if (!mbar_wait(&afull[sa], (t / WSA) & 1)) {
                     ok = false;
                     break;
                 }
-                tc_fence_after();
                 const uint32_t a0 = smem_u32(abase + (size_t)sa * WA_BYTES);
-                const uint32_t b0 = smem_u32(lbase + (size_t)s * L.l_bytes);
 #pragma unroll
-                for (int ks = 0; ks < WJ / 16; ++ks) {
-                    const uint32_t koff = (uint32_t)ks * 256u;
-                    const uint64_t ad = make_desc(a0 + koff, 128, WSBO);
-                    const uint32_t acc = (t == 0 && ks == 0) ? 0u : 1u;
-                    mma_f16(tmem, ad, make_desc(b0 + koff, 128, WSBO), idesc0, acc);
-                    mma_f16(tmem + W_HALF, ad, make_desc(b0 + (W_HALF / 8) * WSBO + koff, 128, WSBO), idesc1, acc);
+                for (int h = 0; h < 2; ++h) {
+                    const int m = 2 * t + h, s = m % SL;
+                    if (!mbar_wait(&full[s], (m / SL) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t b0 = smem_u32(lbase + (size_t)s * L.l_bytes);
+#pragma unroll
+                    for (int ks = 0; ks < WJ / 16; ++ks) {
+                        const uint32_t koff = (uint32_t)ks * 256u;
+                        mma_f16(tmem + (h ? (uint32_t)W_HALF : 0u), make_desc(a0 + koff, 128, WSBO),
+                                make_desc(b0 + koff, 128, WSBO), h ? idesc1 : idesc0, (t == 0 && ks == 0) ? 0u : 1u);
+                    }
+                    mma_commit(&empty[s]);
                 }
-                mma_commit(&empty[s]);
                 mma_commit(&aempty[sa]);
             }
             if (!ok) atomicOr(s_err, ERR_TIMEOUT);
@@ -173,13 +211,14 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
             }
         bool ok = true;
         for (int t = 0; t < T; ++t) {
-            const int s = t % SL, sa = t & 1;
-            if (!mbar_wait(&full[s], (t / SL) & 1) || (t >= 2 && !mbar_wait(&aempty[sa], ((t >> 1) - 1) & 1))) {
+            const int sx = t % WXS, sa = t % WSA;
+            if (!mbar_wait(&xfull[sx], (t / WXS) & 1) ||
+                (t >= WSA && !mbar_wait(&aempty[sa], ((t / WSA) - 1) & 1))) {
                 ok = false;
                 break;
             }
             uint8_t *ast = abase + (size_t)sa * WA_BYTES;
-            const float *xs = reinterpret_cast<const float *>(lbase + (size_t)s * L.l_bytes + L.b_bytes);
+            const float *xs = reinterpret_cast<const float *>(xbase + (size_t)sx * L.x_bytes);
             float2 xj[8][4];
 #pragma unroll
             for (int a = 0; a < 8; ++a) {
@@ -192,6 +231,7 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
                     xj[a][3] = make_float2(hi4.z, hi4.w);
                 }
             }
+            mbar_arrive(&xempty[sx]);  // coordinates are in registers: the stage may be refilled
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 uint32_t w[4];
@@ -312,7 +352,7 @@ __global__ void wide_image_kernel(const float *V, int64_t n, int c, int N, int n
 }
 
 int wide_stages(int N, int d) {
-    for (int s = 4; s >= 2; --s)
+    for (int s = 8; s >= 4; --s)
         if (make_wide_layout(N, d, s).total <= 225 * 1024) return s;
     return 0;
 }
