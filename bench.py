@@ -38,6 +38,23 @@ UNIT = "estimates/s"
 SMS, SM_MHZ_MAX, FP32_PER_CLK, EX2_PER_CLK, SQRT_PER_CLK = 152, 2070.0, 128, 32, 16
 
 
+# DRAM traffic of one launch of the dominant kernel (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum, one pass, n = 2^20, 16 columns, hi/lo fp16: 1.08 GB read +
+# 0.72 GB written), valid only for the kernel sources it was taken on (first 16 hex
+# digits of their sha256); reported as null once those sources change.
+KZ_SYM_TRAFFIC = {"bytes": 1.08e9 + 0.72306e9, "sources": {"paper_2405_03474_gb300/csrc/kz_sym.cu": "c0d89ae5a5bca8db",
+                                                         "paper_2405_03474_gb300/csrc/tc_common.cuh": "c44a6c5e85217efc"}}
+
+
+def measured_traffic(record):
+    import hashlib
+    for rel, digest in record["sources"].items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != digest:
+                return None
+    return record["bytes"]
+
+
 def pair_peak_gps(kind, d):
     """Peak kernel-pair evaluations per second (Gpair/s) of the ALU roofline."""
     if kind == "matern52":
@@ -360,6 +377,12 @@ def run_ours(args, rank, world, local_rank, pool):
         return out
 
     sym_roof, tc_roof = roof("kz_sym_kernel"), roof("kz_tc_kernel")
+    if sym_roof:
+        sym_roof["traffic"] = measured_traffic(KZ_SYM_TRAFFIC)
+        sym_roof["traffic_note"] = ("DRAM bytes per launch from one ncu capture (n=2^20, 16 columns); the "
+                                    "algorithmic DRAM bytes of a matrix-free launch are only its inputs and "
+                                    "output (X tiles, V image, W: ~0.2 GB); the rest is L2 spill of the V "
+                                    "image and W at this n")
     dominant, other = (sym_roof, tc_roof) if (sym_roof and (not tc_roof or per_kernel["kz_sym_kernel"][0] >=
                                                             per_kernel["kz_tc_kernel"][0])) else (tc_roof, sym_roof)
     res = results[-1]
