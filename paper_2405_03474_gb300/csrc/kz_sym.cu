@@ -380,8 +380,7 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                uint32_t w[4];
-                float2 f[4];
+                uint32_t w[4], l[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     float2 u = make_float2(0.f, 0.f);
@@ -392,22 +391,15 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
                             u = __ffma2_rn(dv, dv, u);
                         }
                     }
-                    f[q] = kval2<KIND>(u);
-                    w[q] = pack2<BF16>(f[q].x, f[q].y);
+                    const float2 f = kval2<KIND>(u);
+                    if (NPROD == 3) split_f16(f, w[q], l[q]);
+                    else w[q] = pack2<BF16>(f.x, f.y);
                 }
                 const int r = rg + 32 * k;
                 const size_t off = (size_t)(r >> 3) * CORE_SBO + (size_t)kq * 128 + (size_t)(r & 7) * 16;
                 *reinterpret_cast<uint4 *>(ast + off) = make_uint4(w[0], w[1], w[2], w[3]);
-                if (NPROD == 3) {
-                    const float2 m1 = make_float2(-1.f, -1.f);
-                    uint32_t l[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float2 rq = __ffma2_rn(unpack2<BF16>(w[q]), m1, f[q]);
-                        l[q] = pack2<BF16>(rq.x, rq.y);
-                    }
+                if (NPROD == 3)
                     *reinterpret_cast<uint4 *>(ast + HALF_TILE + off) = make_uint4(l[0], l[1], l[2], l[3]);
-                }
             }
             fence_async_smem();
             // D' buffer (b - 2) & 1 is released before this tile's MMA needs it

@@ -144,6 +144,18 @@ __device__ __forceinline__ float2 unpack2(uint32_t u) {
     }
 }
 
+// hi/lo split of two kernel values for the fp16 x3 products: hi = f with its 13 low
+// mantissa bits cleared (11 significant bits, exact in fp16 over its normal range),
+// lo = f - hi (exact in fp32, |lo| < 2^-10 |f|), both packed to fp16.  Masking takes
+// the ALU pipe instead of a round trip fp32 -> fp16 -> fp32 on the FMA pipe.
+__device__ __forceinline__ void split_f16(float2 f, uint32_t &hi, uint32_t &lo) {
+    const float2 h = make_float2(__uint_as_float(__float_as_uint(f.x) & 0xFFFFE000u),
+                                 __uint_as_float(__float_as_uint(f.y) & 0xFFFFE000u));
+    const float2 l = __ffma2_rn(h, make_float2(-1.f, -1.f), f);
+    hi = pack2<false>(h.x, h.y);
+    lo = pack2<false>(l.x, l.y);
+}
+
 // ---- raw MUFU ops (one instruction each; packed f32x2 arithmetic uses the
 // sm_100 float2 builtins __fadd2_rn / __ffma2_rn / __fmul2_rn)
 __device__ __forceinline__ float mufu_ex2_neg(float x) {  // 2^-x
