@@ -10,9 +10,13 @@
 // (one 256-column half, 32 KB, per stage, each with its own barrier, so several
 // loads are in flight and each half's MMAs start when it lands; the CTAs of one
 // wave walk the j-tiles in the same order, so each tile is read from L2 by all of
-// them).  D accumulates over all j-tiles in tensor memory (fp32, no drains: the
-// single-product forms are for the sketch, whose accuracy is set by fp16 rounding
-// of K and V) and is written once at the end.  Every mbarrier wait is bounded.
+// them).  D accumulates over the CTA's j-tiles in tensor memory (fp32, no drains:
+// the single-product forms are for the sketch, whose accuracy is set by fp16
+// rounding of K and V).  Large n splits the j-tiles into chunks of WCHUNK (64 MB of
+// operand image at 512 columns), one grid row per chunk in launch order, so the
+// CTAs resident at one time stream one chunk that stays in L2; each CTA then adds
+// its partial rows into W (zeroed first) with 16-byte vector reductions.  Every
+// mbarrier wait is bounded.
 #include <math.h>
 
 #include <algorithm>
@@ -34,6 +38,7 @@ constexpr int WA_BYTES = WM * WJ * 2;   // one 128 x 64 tile of halves
 constexpr int WSBO = (WJ / 8) * 128;    // 1024: byte step between 8-row groups
 constexpr int W_MAXN = 512;
 constexpr int W_HALF = 256;             // MMA N of the first half
+constexpr int WCHUNK = 1024;            // j-tiles per grid row when the j range is split
 constexpr int WSA = 4;                  // K-tile stages (evaluation runs up to 4 tiles ahead of the MMA)
 constexpr int WXS = 8;                  // point-coordinate stages (their own ring, so the evaluation
                                         // does not wait for the operand image)
@@ -46,6 +51,8 @@ struct WideParams {
     float *W;
     int64_t n;
     int d, c, N, ntiles;
+    int nchunks;         // > 1: partial sums over j-chunks, added into a zeroed W
+    int vec_ok;          // W rows 16-byte aligned (c % 4 == 0 and W aligned)
     float variance, noise;
     int *err;
 };
@@ -91,7 +98,8 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int dd = DC > 0 ? DC : p.d;
-    const int T = p.ntiles;
+    const int tbeg = blockIdx.y * WCHUNK;
+    const int T = min(p.ntiles - tbeg, p.nchunks > 1 ? WCHUNK : p.ntiles);  // j-tiles of this CTA
     const int SL = L.sl;
     const int64_t row0 = (int64_t)blockIdx.x * WM;
 
@@ -139,7 +147,7 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
                 uint8_t *st = lbase + (size_t)s * L.l_bytes;
                 const uint32_t hb = (uint32_t)(h ? L.h1_bytes : L.h0_bytes);
                 mbar_expect_tx(&full[s], hb);
-                bulk_g2s(st, p.img + (size_t)t * tile_bytes + (h ? (size_t)L.h0_bytes : 0), hb, &full[s]);
+                bulk_g2s(st, p.img + (size_t)(tbeg + t) * tile_bytes + (h ? (size_t)L.h0_bytes : 0), hb, &full[s]);
             }
             for (int u = std::max(0, m - SL); u < m; ++u)
                 if (!mbar_wait(&full[u % SL], (u / SL) & 1)) atomicOr(s_err, ERR_TIMEOUT);
@@ -154,7 +162,7 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
                     break;
                 }
                 mbar_expect_tx(&xfull[s], xb);
-                bulk_g2s(xbase + (size_t)s * xb, p.Xp + (size_t)t * WJ * dd, xb, &xfull[s]);
+                bulk_g2s(xbase + (size_t)s * xb, p.Xp + (size_t)(tbeg + t) * WJ * dd, xb, &xfull[s]);
             }
             for (int u = std::max(0, t - WXS); u < t; ++u)
                 if (!mbar_wait(&xfull[u % WXS], (u / WXS) & 1)) atomicOr(s_err, ERR_TIMEOUT);
@@ -268,11 +276,29 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
                 float v[8];
                 tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c8, v);
                 if (i < p.n) {
+                    float o[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int col = c8 + q;
-                        if (col < p.c)
-                            p.W[i * p.c + col] = v[q] * p.variance * p.colinv[col] + p.noise * p.V[i * p.c + col];
+                        o[q] = col < p.c ? v[q] * p.variance * p.colinv[col] +
+                                               (blockIdx.y == 0 ? p.noise * p.V[i * p.c + col] : 0.f)
+                                         : 0.f;
+                    }
+                    float *dst = p.W + i * p.c + c8;
+                    if (p.nchunks == 1) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            if (c8 + q < p.c) dst[q] = o[q];
+                    } else if (p.vec_ok) {
+#pragma unroll
+                        for (int g = 0; g < 2; ++g)
+                            if (c8 + 4 * g < p.c)
+                                atomicAdd(reinterpret_cast<float4 *>(dst + 4 * g),
+                                          make_float4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]));
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            if (c8 + q < p.c) atomicAdd(dst + q, o[q]);
                     }
                 }
             }
@@ -367,7 +393,7 @@ int launch_wide(const WideParams &p, const WideLayout &L, int nblocks, cudaStrea
     }
     const double nn = (double)p.n * (double)p.n;
     const int slot = prof_begin_launch(st, PROF_KZ_TC, nn, 2.0 * nn * p.N);
-    fn<<<nblocks, WTHREADS, L.total, st>>>(p, L);
+    fn<<<dim3(nblocks, p.nchunks), WTHREADS, L.total, st>>>(p, L);
     prof_end_launch(st, slot);
     return check_launch("kz_wide_kernel");
 }
@@ -447,6 +473,9 @@ int kz_wide(const float *Xs, int64_t n, int d, int kind, double variance, double
         p.c = c;
         p.N = N;
         p.ntiles = (int)ntiles;
+        p.nchunks = (int)((ntiles + WCHUNK - 1) / WCHUNK);
+        p.vec_ok = (reinterpret_cast<uintptr_t>(W) % 16 == 0) && (c % 4 == 0);
+        if (p.nchunks > 1) LD_CHECK_CUDA(cudaMemsetAsync(W, 0, sizeof(float) * (size_t)n * c, st));
         p.variance = (float)variance;
         p.noise = (float)noise;
         p.err = err;

@@ -105,6 +105,20 @@ def test_kz_wide_sketch_sampled_rows_at_large_n():
     assert relerr(W[rows], ref) < TC_TOL["f16_tc"]
 
 
+@pytest.mark.parametrize("c", [270, 512])
+def test_kz_wide_two_j_chunks_sampled_rows(c):
+    # n just over 1024 j-tiles of 64 points: two grid rows whose partial sums are added into W
+    # (vector reductions for c % 4 == 0, per-element ones for c = 270)
+    n, d = 66000, 3
+    X = inputs.points(n, d, "uniform", seed=4)
+    V = inputs.gaussian(n, c, seed=9)
+    k = api.Kernel(api.RBF, 0.05, 1.3, 2e-2)
+    W = host(api.ld_kz(cuda(X), cuda(V, torch.float32), k, "f16_tc"))
+    rows = np.concatenate([np.random.default_rng(5).choice(n, 10, replace=False), [0, n - 1]])
+    ref = kernels.kz_rows(X, V, rows, api.RBF, 0.05, 1.3, 2e-2)
+    assert relerr(W[rows], ref) < TC_TOL["f16_tc"]
+
+
 def test_kz_f16x3_sampled_rows_at_large_n():
     n, d, c = 1 << 18, 4, 16
     X = inputs.points(n, d, "uniform", seed=0)
