@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
             const uint32_t idesc_w = make_idesc(BR, (int)NW, BF16 ? 1u : 0u, 0u);  // B = [V_hi | V_lo]
             const uint32_t idesc_wt = make_idesc(BR, (int)NW, BF16 ? 1u : 0u, 1u);
             bool ok = mbar_wait(vfull, 0);
-            const uint32_t vi0 = smem_u32(vimg);
+            const uint64_t dvi = make_desc(smem_u32(vimg), 128, CORE_SBO);
             for (int b = 0; b < T && ok; ++b) {
                 const int s = b % SL, sa = b & 1;
                 const int k = b / SKCH;
@@ -222,35 +222,32 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
                     break;
                 }
                 tc_fence_after();
+                // Descriptors advance by a constant per K-step (the start address field is
+                // address >> 4 and no step carries out of it), so they are formed once.
                 const uint32_t a0 = smem_u32(abase + (size_t)sa * L.a_bytes);
                 const uint32_t b0 = smem_u32(lbase + (size_t)s * L.l_bytes);
                 // D_I += K_IJ V_J: A K-major (lbo = 128 along j, sbo = 2048 along i)
+                const uint64_t dah = make_desc(a0, 128, CORE_SBO);
+                const uint64_t dal = dah + (uint64_t)(HALF_TILE >> 4);
+                const uint64_t dbh = make_desc(b0, 128, CORE_SBO);  // N = NW spans hi, lo
 #pragma unroll
                 for (int ks = 0; ks < BR / 16; ++ks) {
-                    const uint32_t koff = (uint32_t)ks * 256u;
-                    const uint64_t ah = make_desc(a0 + koff, 128, CORE_SBO);
-                    const uint64_t bh = make_desc(b0 + koff, 128, CORE_SBO);  // N = NW spans hi, lo
-                    mma_f16(dt, ah, bh, idesc_w, (first && ks == 0) ? 0u : 1u);
-                    if (NPROD == 3) {
-                        const uint64_t al = make_desc(a0 + (uint32_t)HALF_TILE + koff, 128, CORE_SBO);
-                        mma_f16(dt + SN, al, bh, idesc, 1u);
-                    }
+                    const uint64_t step = (uint64_t)(ks * (256 >> 4));
+                    mma_f16(dt, dah + step, dbh + step, idesc_w, (first && ks == 0) ? 0u : 1u);
+                    if (NPROD == 3) mma_f16(dt + SN, dal + step, dbh + step, idesc, 1u);
                 }
                 if (b >= 1) {
                     // D'_J = K_IJ^T V_I: the same tile MN-major (rows j; lbo = 2048 along i,
                     // sbo = 128 along j), B = own V image (K = i)
                     const uint32_t tdt = tmem + doff + (uint32_t)((b & 1) * NW);
+                    const uint64_t dat = make_desc(a0, CORE_SBO, 128);
+                    const uint64_t dalt = dat + (uint64_t)(HALF_TILE >> 4);
 #pragma unroll
                     for (int ks = 0; ks < BR / 16; ++ks) {
-                        const uint32_t koff_t = (uint32_t)ks * (2u * CORE_SBO);
-                        const uint32_t bkoff = (uint32_t)ks * 256u;
-                        const uint64_t ah = make_desc(a0 + koff_t, CORE_SBO, 128);
-                        const uint64_t bh = make_desc(vi0 + bkoff, 128, CORE_SBO);
-                        mma_f16(tdt, ah, bh, idesc_wt, ks == 0 ? 0u : 1u);
-                        if (NPROD == 3) {
-                            const uint64_t al = make_desc(a0 + (uint32_t)HALF_TILE + koff_t, CORE_SBO, 128);
-                            mma_f16(tdt + SN, al, bh, idesc_t, 1u);
-                        }
+                        const uint64_t astep = (uint64_t)(ks * ((2 * CORE_SBO) >> 4));
+                        const uint64_t bstep = (uint64_t)(ks * (256 >> 4));
+                        mma_f16(tdt, dat + astep, dvi + bstep, idesc_wt, ks == 0 ? 0u : 1u);
+                        if (NPROD == 3) mma_f16(tdt + SN, dalt + astep, dvi + bstep, idesc_t, 1u);
                     }
                     mma_commit(&tfull[b & 1]);
                 }

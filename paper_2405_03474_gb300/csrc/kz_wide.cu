@@ -188,12 +188,13 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t b0 = smem_u32(lbase + (size_t)s * L.l_bytes);
+                    const uint64_t da = make_desc(a0, 128, WSBO);
+                    const uint64_t db = make_desc(smem_u32(lbase + (size_t)s * L.l_bytes), 128, WSBO);
 #pragma unroll
                     for (int ks = 0; ks < WJ / 16; ++ks) {
-                        const uint32_t koff = (uint32_t)ks * 256u;
-                        mma_f16(tmem + (h ? (uint32_t)W_HALF : 0u), make_desc(a0 + koff, 128, WSBO),
-                                make_desc(b0 + koff, 128, WSBO), h ? idesc1 : idesc0, (t == 0 && ks == 0) ? 0u : 1u);
+                        const uint64_t step = (uint64_t)(ks * (256 >> 4));  // descriptors advance by a constant
+                        mma_f16(tmem + (h ? (uint32_t)W_HALF : 0u), da + step, db + step, h ? idesc1 : idesc0,
+                                (t == 0 && ks == 0) ? 0u : 1u);
                     }
                     mma_commit(&empty[s]);
                 }
