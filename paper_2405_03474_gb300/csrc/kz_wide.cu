@@ -3,20 +3,20 @@
 //
 // The general kernel keeps two CTAs per SM with at most 256 accumulator columns
 // each, so 512 columns took two launches that each evaluated every kernel value.
-// Here one CTA per SM owns all 512 TMEM columns: the 128 x 64 tile K_IJ is
-// evaluated once by 16 eval warps (2 rows x 8 j per thread, packed f32x2, MUFU
-// sqrt + ex2) and multiplied into both 256-column halves of D by two tcgen05.mma
-// per K-step; the operand image of V streams through a ring of half-tile stages
-// (one 256-column half, 32 KB, per stage, each with its own barrier, so several
-// loads are in flight and each half's MMAs start when it lands; the CTAs of one
-// wave walk the j-tiles in the same order, so each tile is read from L2 by all of
-// them).  D accumulates over the CTA's j-tiles in tensor memory (fp32, no drains:
-// the single-product forms are for the sketch, whose accuracy is set by fp16
-// rounding of K and V).  Large n splits the j-tiles into chunks of WCHUNK (64 MB of
-// operand image at 512 columns), one grid row per chunk in launch order, so the
-// CTAs resident at one time stream one chunk that stays in L2; each CTA then adds
-// its partial rows into W (zeroed first) with 16-byte vector reductions.  Every
-// mbarrier wait is bounded.
+// Here one CTA per SM owns all 512 TMEM columns: the 128 x 128 tile K_IJ is
+// evaluated once by 16 eval warps (4 rows x 8 j per thread, packed f32x2, MUFU
+// sqrt + ex2) into one of two K-tile stages and multiplied into both 256-column
+// halves of D (16 tcgen05.mma per tile).  The operand image of V (64-point tiles,
+// 32 KB per 256-column half) streams through a ring of quarter-tile stages, each
+// with its own barrier, so several loads are in flight and each quarter's MMAs
+// start when it lands; the point coordinates have a ring of their own, fed by a
+// second producer lane.  D accumulates over the CTA's j-tiles in tensor memory
+// (fp32, no drains: the single-product forms are for the sketch, whose accuracy
+// is set by fp16 rounding of K and V).  Large n splits the j-tiles into chunks of
+// WCHUNK (64 MB of operand image at 512 columns), one grid row per chunk in launch
+// order, so the CTAs resident at one time stream one chunk that stays in L2; each
+// CTA then adds its partial rows into W (zeroed first) with 16-byte vector
+// reductions.  Every mbarrier wait is bounded.
 #include <math.h>
 
 #include <algorithm>
@@ -31,37 +31,39 @@ using namespace tc;
 namespace {
 
 constexpr int WM = 128;                 // rows per CTA (MMA M, TMEM lanes)
-constexpr int WJ = 64;                  // j per tile (4 MMA K-steps of 16)
+constexpr int WJ = 64;                  // points per point tile / image tile (4 MMA K-steps)
+constexpr int WT = 128;                 // j per evaluated tile (two point tiles)
 constexpr int WEVAL = 16;               // eval warps
 constexpr int WTHREADS = (WEVAL + 2) * 32;
-constexpr int WA_BYTES = WM * WJ * 2;   // one 128 x 64 tile of halves
-constexpr int WSBO = (WJ / 8) * 128;    // 1024: byte step between 8-row groups
+constexpr int WA_BYTES = WM * WT * 2;   // one 128 x 128 tile of halves
+constexpr int WASBO = (WT / 8) * 128;   // 2048: K-tile byte step between 8-row groups
+constexpr int WSBO = (WJ / 8) * 128;    // 1024: image byte step between 8-column groups
 constexpr int W_MAXN = 512;
 constexpr int W_HALF = 256;             // MMA N of the first half
-constexpr int WCHUNK = 1024;            // j-tiles per grid row when the j range is split
-constexpr int WSA = 4;                  // K-tile stages (evaluation runs up to 4 tiles ahead of the MMA)
-constexpr int WXS = 8;                  // point-coordinate stages (their own ring, so the evaluation
-                                        // does not wait for the operand image)
+constexpr int WSA = 2;                  // K-tile stages
+constexpr int WXS = 4;                  // point-coordinate stages
+constexpr int WCHUNK = 512;             // evaluated j-tiles per grid row when the j range is split
 
 struct WideParams {
     const float *Xp;     // per 64-point tile: d x 64 floats, far-padded, log2 e folded in
-    const uint8_t *img;  // per 64-point tile: N x 64 halves, canonical K-major
+    const uint8_t *img;  // per 64-point tile: N x 64 halves, canonical K-major (256-column halves)
     const float *V;      // n x c
     const float *colinv; // 1 / column scale (N)
     float *W;
     int64_t n;
-    int d, c, N, ntiles;
-    int nchunks;         // > 1: partial sums over j-chunks, added into a zeroed W
-    int vec_ok;          // W rows 16-byte aligned (c % 4 == 0 and W aligned)
+    int d, c, N, ntiles;  // ntiles: evaluated 128-point j-tiles (point tiles are twice as many)
+    int nchunks;          // > 1: partial sums over j-chunks, added into a zeroed W
+    int vec_ok;           // W rows 16-byte aligned (c % 4 == 0 and W aligned)
     float variance, noise;
     int *err;
 };
 
-// Ring of SL half-tile stages: stage m % SL holds half h = m % 2 of j-tile m / 2
-// (h0_bytes = 256 columns, h1_bytes = N - 256); the point coordinates of the
-// j-tiles (x_bytes each) have a ring of WXS stages of their own.
+// Ring of SL quarter stages: stage m % SL holds 256-column half h = m % 2 of point tile
+// 2 (m / 4) + (m / 2) % 2 (h0_bytes for the first half, h1_bytes = (N - 256) x 64 x 2 for
+// the second); the coordinates of each evaluated tile (two point tiles, x_bytes) have a
+// ring of WXS stages of their own.
 struct WideLayout {
-    int sl, h0_bytes, h1_bytes, x_bytes, l_bytes, a_off, x_off, l_off, total;
+    int sl, h0_bytes, h1_bytes, x_bytes, a_off, x_off, l_off, total;
 };
 
 WideLayout make_wide_layout(int N, int d, int sl) {
@@ -69,12 +71,11 @@ WideLayout make_wide_layout(int N, int d, int sl) {
     L.sl = sl;
     L.h0_bytes = W_HALF * WJ * 2;
     L.h1_bytes = (N - W_HALF) * WJ * 2;
-    L.x_bytes = WJ * d * 4;
-    L.l_bytes = L.h0_bytes;
+    L.x_bytes = WT * d * 4;
     L.a_off = 1024;
     L.x_off = L.a_off + WSA * WA_BYTES;
     L.l_off = L.x_off + ((WXS * L.x_bytes + 1023) / 1024) * 1024;
-    L.total = L.l_off + sl * L.l_bytes + 1024;
+    L.total = L.l_off + sl * L.h0_bytes + 1024;
     return L;
 }
 
@@ -133,26 +134,27 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
     const uint32_t tmem = *tmem_slot;
 
     if (warp == WEVAL + 1) {
-        // ---------------- producer: operand image and point tile of each j-tile
         if (lane == 0) {
+            // ---------------- producer: quarters (point tile, 256-column half) of the image
             const size_t tile_bytes = (size_t)L.h0_bytes + L.h1_bytes;
-            const int M = 2 * T;  // half-tile loads
+            const int M = 4 * T;
             int m = 0;
             for (; m < M; ++m) {
-                const int s = m % SL, t = m >> 1, h = m & 1;
+                const int s = m % SL, h = m & 1;
+                const int64_t it = 2 * (int64_t)(tbeg + (m >> 2)) + ((m >> 1) & 1);
                 if (m >= SL && !mbar_wait(&empty[s], ((m / SL) - 1) & 1)) {
                     atomicOr(s_err, ERR_TIMEOUT);
                     break;
                 }
-                uint8_t *st = lbase + (size_t)s * L.l_bytes;
                 const uint32_t hb = (uint32_t)(h ? L.h1_bytes : L.h0_bytes);
                 mbar_expect_tx(&full[s], hb);
-                bulk_g2s(st, p.img + (size_t)(tbeg + t) * tile_bytes + (h ? (size_t)L.h0_bytes : 0), hb, &full[s]);
+                bulk_g2s(lbase + (size_t)s * L.h0_bytes, p.img + (size_t)it * tile_bytes + (h ? (size_t)L.h0_bytes : 0),
+                         hb, &full[s]);
             }
             for (int u = std::max(0, m - SL); u < m; ++u)
                 if (!mbar_wait(&full[u % SL], (u / SL) & 1)) atomicOr(s_err, ERR_TIMEOUT);
         } else if (lane == 1) {
-            // point coordinates of each j-tile, ahead of the evaluation
+            // ---------------- producer: coordinates of each evaluated tile (two point tiles)
             const uint32_t xb = (uint32_t)L.x_bytes;
             int t = 0;
             for (; t < T; ++t) {
@@ -162,13 +164,13 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
                     break;
                 }
                 mbar_expect_tx(&xfull[s], xb);
-                bulk_g2s(xbase + (size_t)s * xb, p.Xp + (size_t)(tbeg + t) * WJ * dd, xb, &xfull[s]);
+                bulk_g2s(xbase + (size_t)s * xb, p.Xp + (size_t)(tbeg + t) * WT * dd, xb, &xfull[s]);
             }
             for (int u = std::max(0, t - WXS); u < t; ++u)
                 if (!mbar_wait(&xfull[u % WXS], (u / WXS) & 1)) atomicOr(s_err, ERR_TIMEOUT);
         }
     } else if (warp == WEVAL) {
-        // ---------------- MMA issuer: D[:, 0:256] and D[:, 256:N] += K_IJ V_J
+        // ---------------- MMA issuer: D[:, 0:256] and D[:, 256:N] += K_IJ V_J, per quarter
         if (lane == 0) {
             const uint32_t idesc0 = make_idesc(WM, W_HALF, BF16 ? 1u : 0u);
             const uint32_t idesc1 = make_idesc(WM, p.N - W_HALF, BF16 ? 1u : 0u);
@@ -179,22 +181,23 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
                     ok = false;
                     break;
                 }
-                const uint32_t a0 = smem_u32(abase + (size_t)sa * WA_BYTES);
+                const uint64_t da = make_desc(smem_u32(abase + (size_t)sa * WA_BYTES), 128, WASBO);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int m = 2 * t + h, s = m % SL;
+                for (int q = 0; q < 4; ++q) {
+                    const int g = q >> 1, h = q & 1;  // j half (point tile) and column half
+                    const int m = 4 * t + q, s = m % SL;
                     if (!mbar_wait(&full[s], (m / SL) & 1)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t da = make_desc(a0, 128, WSBO);
-                    const uint64_t db = make_desc(smem_u32(lbase + (size_t)s * L.l_bytes), 128, WSBO);
+                    const uint64_t db = make_desc(smem_u32(lbase + (size_t)s * L.h0_bytes), 128, WSBO);
+                    const uint64_t dag = da + (uint64_t)(g * ((WJ / 8) * 128 >> 4));  // 64 j further along K
 #pragma unroll
                     for (int ks = 0; ks < WJ / 16; ++ks) {
                         const uint64_t step = (uint64_t)(ks * (256 >> 4));  // descriptors advance by a constant
-                        mma_f16(tmem + (h ? (uint32_t)W_HALF : 0u), da + step, db + step, h ? idesc1 : idesc0,
-                                (t == 0 && ks == 0) ? 0u : 1u);
+                        mma_f16(tmem + (h ? (uint32_t)W_HALF : 0u), dag + step, db + step, h ? idesc1 : idesc0,
+                                (t == 0 && g == 0 && ks == 0) ? 0u : 1u);
                     }
                     mma_commit(&empty[s]);
                 }
@@ -205,15 +208,14 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
             if (!mbar_wait(done, 0)) atomicOr(s_err, ERR_TIMEOUT);
         }
     } else {
-        // ---------------- eval warps: rows 64 h + lane + 32 k (k = 0, 1), j in [8 kq, 8 kq + 8)
-        const int kq = warp & 7;
-        const int h = warp >> 3;
-        float2 xr[2][8];
+        // ---------------- eval warps: rows lane + 32 k (k = 0..3), j in [8 warp, 8 warp + 8)
+        const int kq = warp;
+        float2 xr[4][8];
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < 4; ++k)
 #pragma unroll
             for (int a = 0; a < 8; ++a) {
-                const int64_t i = row0 + 64 * h + lane + 32 * k;
+                const int64_t i = row0 + lane + 32 * k;
                 const float v = (a < dd && i < p.n) ? -p.Xp[(size_t)(i / WJ) * WJ * dd + a * WJ + (i % WJ)]
                                                     : (a < dd ? -1e18f : 0.f);
                 xr[k][a] = make_float2(v, v);
@@ -227,13 +229,15 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
                 break;
             }
             uint8_t *ast = abase + (size_t)sa * WA_BYTES;
-            const float *xs = reinterpret_cast<const float *>(xbase + (size_t)sx * L.x_bytes);
+            // this warp's 8 points lie in point tile kq / 8 of the two
+            const float *xs = reinterpret_cast<const float *>(xbase + (size_t)sx * L.x_bytes) +
+                              (kq >> 3) * WJ * dd + (kq & 7) * 8;
             float2 xj[8][4];
 #pragma unroll
             for (int a = 0; a < 8; ++a) {
                 if (a < dd) {
-                    const float4 lo4 = *reinterpret_cast<const float4 *>(xs + a * WJ + kq * 8);
-                    const float4 hi4 = *reinterpret_cast<const float4 *>(xs + a * WJ + kq * 8 + 4);
+                    const float4 lo4 = *reinterpret_cast<const float4 *>(xs + a * WJ);
+                    const float4 hi4 = *reinterpret_cast<const float4 *>(xs + a * WJ + 4);
                     xj[a][0] = make_float2(lo4.x, lo4.y);
                     xj[a][1] = make_float2(lo4.z, lo4.w);
                     xj[a][2] = make_float2(hi4.x, hi4.y);
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
             }
             mbar_arrive(&xempty[sx]);  // coordinates are in registers: the stage may be refilled
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < 4; ++k) {
                 uint32_t w[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -257,14 +261,14 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
                     const float2 f = kval2<KIND>(u);
                     w[q] = pack2<BF16>(f.x, f.y);
                 }
-                const int r = 64 * h + lane + 32 * k;
-                const size_t off = (size_t)(r >> 3) * WSBO + (size_t)kq * 128 + (size_t)(r & 7) * 16;
+                const int r = lane + 32 * k;
+                const size_t off = (size_t)(r >> 3) * WASBO + (size_t)kq * 128 + (size_t)(r & 7) * 16;
                 *reinterpret_cast<uint4 *>(ast + off) = make_uint4(w[0], w[1], w[2], w[3]);
             }
             fence_async_smem();
             mbar_arrive(&afull[sa]);
         }
-        // ---------------- epilogue: W = variance * colinv * D + noise * V
+        // ---------------- epilogue: W (+)= variance * colinv * D (+ noise * V in the first chunk)
         const bool got = ok && mbar_wait(done, 0);
         tc_fence_after();
         if (!got) {
@@ -384,6 +388,9 @@ int wide_stages(int N, int d) {
     return 0;
 }
 
+// evaluated 128-point j-tiles; the point tiles and image tiles (64 points) are twice as many
+int64_t wide_tiles(int64_t n) { return (n + WT - 1) / WT; }
+
 template <int KIND, int DC, bool BF16>
 int launch_wide(const WideParams &p, const WideLayout &L, int nblocks, cudaStream_t st) {
     auto fn = kz_wide_kernel<KIND, DC, BF16>;
@@ -421,12 +428,12 @@ bool kz_wide_eligible(int64_t n, int d, int c, int precision) {
 
 size_t kz_wide_workspace(int64_t n, int d, int c, int precision) {
     (void)precision;
-    const int64_t ntiles = (n + WJ - 1) / WJ;
+    const int64_t npt = 2 * wide_tiles(n);
     const int N = wide_N(c);
     Arena a;
     a.measuring = true;
-    a.take<float>((size_t)ntiles * WJ * d);
-    a.take<uint8_t>((size_t)ntiles * N * WJ * 2);
+    a.take<float>((size_t)npt * WJ * d);
+    a.take<uint8_t>((size_t)npt * N * WJ * 2);
     a.take<float>(W_MAXN);
     a.take<float>(W_MAXN);
     a.take<float>((size_t)256 * W_MAXN);
@@ -436,12 +443,12 @@ size_t kz_wide_workspace(int64_t n, int d, int c, int precision) {
 
 int kz_wide(const float *Xs, int64_t n, int d, int kind, double variance, double noise, const float *V,
             float *W, int c, int precision, Arena &ws, cudaStream_t st) {
-    const int64_t ntiles = (n + WJ - 1) / WJ;
+    const int64_t ntiles = wide_tiles(n), npt = 2 * ntiles;
     const int N = wide_N(c);
     const bool bf16 = precision == LD_BF16_TC;
     const size_t mark = ws.off;
-    float *Xp = ws.take<float>((size_t)ntiles * WJ * d);
-    uint8_t *img = ws.take<uint8_t>((size_t)ntiles * N * WJ * 2);
+    float *Xp = ws.take<float>((size_t)npt * WJ * d);
+    uint8_t *img = ws.take<uint8_t>((size_t)npt * N * WJ * 2);
     float *scale = ws.take<float>(W_MAXN);
     float *colinv = ws.take<float>(W_MAXN);
     float *part = ws.take<float>((size_t)256 * W_MAXN);
@@ -453,14 +460,14 @@ int kz_wide(const float *Xs, int64_t n, int d, int kind, double variance, double
     }
     int code = [&]() -> int {
         const float factor = kind == LD_RBF ? 1.2011224087864498f : 1.4426950408889634f;
-        const int64_t cnt = ntiles * WJ * d;
-        wide_point_tiles_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(Xs, n, d, factor, ntiles, Xp);
+        const int64_t cnt = npt * WJ * d;
+        wide_point_tiles_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(Xs, n, d, factor, npt, Xp);
         wide_colmax_kernel<<<256, W_MAXN, 0, st>>>(V, n, c, N, part);
         wide_colscale_kernel<<<1, W_MAXN, 0, st>>>(part, 256, N, scale, colinv);
-        const int64_t nthr = ntiles * N * (WJ / 8);
+        const int64_t nthr = npt * N * (WJ / 8);
         const unsigned gb = (unsigned)((nthr + 255) / 256);
-        if (bf16) wide_image_kernel<true><<<gb, 256, 0, st>>>(V, n, c, N, (int)ntiles, scale, img);
-        else wide_image_kernel<false><<<gb, 256, 0, st>>>(V, n, c, N, (int)ntiles, scale, img);
+        if (bf16) wide_image_kernel<true><<<gb, 256, 0, st>>>(V, n, c, N, (int)npt, scale, img);
+        else wide_image_kernel<false><<<gb, 256, 0, st>>>(V, n, c, N, (int)npt, scale, img);
         LD_TRY(check_launch("kz_wide prep", 4));
         LD_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
         WideParams p;
