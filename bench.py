@@ -39,11 +39,11 @@ SMS, SM_MHZ_MAX, FP32_PER_CLK, EX2_PER_CLK, SQRT_PER_CLK = 152, 2070.0, 128, 32,
 
 
 # DRAM traffic of one launch of the dominant kernel (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum, one pass, n = 2^20, 16 columns, hi/lo fp16: 1.08 GB read +
-# 0.72 GB written), valid only for the kernel sources it was taken on (first 16 hex
+# dram__bytes_write.sum, one pass, n = 2^20, 16 columns, hi/lo fp16: 1.04 GB read +
+# 0.75 GB written), valid only for the kernel sources it was taken on (first 16 hex
 # digits of their sha256); reported as null once those sources change.
-KZ_SYM_TRAFFIC = {"bytes": 1.08e9 + 0.72306e9, "sources": {"paper_2405_03474_gb300/csrc/kz_sym.cu": "c0d89ae5a5bca8db",
-                                                         "paper_2405_03474_gb300/csrc/tc_common.cuh": "c44a6c5e85217efc"}}
+KZ_SYM_TRAFFIC = {"bytes": 1.04e9 + 0.7521e9, "sources": {"paper_2405_03474_gb300/csrc/kz_sym.cu": "2a345fb65667e300",
+                                                         "paper_2405_03474_gb300/csrc/tc_common.cuh": "efe385d1449bd0a8"}}
 
 
 def measured_traffic(record):
@@ -319,7 +319,7 @@ def run_ours(args, rank, world, local_rank, pool):
                                       ctypes.c_double())
     lib.ld_profile_end(ctypes.byref(kz_ms), ctypes.byref(kz_n), ctypes.byref(kz_pairs), ctypes.byref(kz_flops))
     per_kernel = {}
-    for kid, kname_ in ((1, "kz_sym_kernel"), (0, "kz_tc_kernel")):
+    for kid, kname_ in ((1, "kz_sym_kernel"), (4, "kz_wide_kernel"), (0, "kz_tc_kernel")):
         m_, n_, p_, f_ = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
         lib.ld_profile_kernel(kid, ctypes.byref(m_), ctypes.byref(n_), ctypes.byref(p_), ctypes.byref(f_))
         per_kernel[kname_] = (m_.value, n_.value, p_.value, f_.value)
@@ -376,15 +376,16 @@ def run_ours(args, rank, world, local_rank, pool):
             out["tensor_frac_of_measured_bf16"] = out["tensor_tflops"] / tc_peak
         return out
 
-    sym_roof, tc_roof = roof("kz_sym_kernel"), roof("kz_tc_kernel")
+    sym_roof = roof("kz_sym_kernel")
     if sym_roof:
         sym_roof["traffic"] = measured_traffic(KZ_SYM_TRAFFIC)
         sym_roof["traffic_note"] = ("DRAM bytes per launch from one ncu capture (n=2^20, 16 columns); the "
                                     "algorithmic DRAM bytes of a matrix-free launch are only its inputs and "
                                     "output (X tiles, V image, W: ~0.2 GB); the rest is L2 spill of the V "
                                     "image and W at this n")
-    dominant, other = (sym_roof, tc_roof) if (sym_roof and (not tc_roof or per_kernel["kz_sym_kernel"][0] >=
-                                                            per_kernel["kz_tc_kernel"][0])) else (tc_roof, sym_roof)
+    roofs = [r for r in (sym_roof, roof("kz_wide_kernel"), roof("kz_tc_kernel")) if r]
+    roofs.sort(key=lambda r: -r["share_of_step"])
+    dominant, others = (roofs[0] if roofs else None), roofs[1:]
     res = results[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -405,9 +406,9 @@ def run_ours(args, rank, world, local_rank, pool):
         "estimate": {"logdet": res["logdet"], "logdet_P": res["logdet_P"], "std_err": res["std_err"],
                      "iters": res["iters"], "max_resid": res["max_resid"][:w["order"]]},
         "roofline": dominant,
-        "roofline_other_kernel": other,
+        "roofline_other_kernels": others,
         "kernel_products": {"launches": kz_n.value, "device_ms": kz_ms.value, "share_of_step": kz_ms.value / total_ms,
-                            "product_pairs_per_s": (per_kernel["kz_sym_kernel"][1] + per_kernel["kz_tc_kernel"][1])
+                            "product_pairs_per_s": sum(v[1] for v in per_kernel.values())
                             * float(n) * n / (kz_ms.value / 1e3) if kz_ms.value else None},
         "clocks": clk,
         "gpu_launches": int(launches),

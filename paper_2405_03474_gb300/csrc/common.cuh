@@ -58,7 +58,7 @@ inline int check_launch(const char *what, int launches = 1) {
 // Optional timing of the kernel-product launches (CUDA events on the launch
 // stream), enabled between ld_profile_begin and ld_profile_end.
 // kernel ids of the profile totals (ld_profile_kernel)
-enum { PROF_KZ_TC = 0, PROF_KZ_SYM = 1, PROF_KZ_SIMT = 2, PROF_DENSE = 3, PROF_KERNELS = 4 };
+enum { PROF_KZ_TC = 0, PROF_KZ_SYM = 1, PROF_KZ_SIMT = 2, PROF_DENSE = 3, PROF_KZ_WIDE = 4, PROF_KERNELS = 5 };
 int prof_begin_launch(cudaStream_t st, int kernel, double pairs, double mma_flops);  // -1 when off
 void prof_end_launch(cudaStream_t st, int slot);
 

@@ -400,7 +400,7 @@ int launch_wide(const WideParams &p, const WideLayout &L, int nblocks, cudaStrea
         return LD_ERR_CUDA;
     }
     const double nn = (double)p.n * (double)p.n;
-    const int slot = prof_begin_launch(st, PROF_KZ_TC, nn, 2.0 * nn * p.N);
+    const int slot = prof_begin_launch(st, PROF_KZ_WIDE, nn, 2.0 * nn * p.N);
     fn<<<dim3(nblocks, p.nchunks), WTHREADS, L.total, st>>>(p, L);
     prof_end_launch(st, slot);
     return check_launch("kz_wide_kernel");
