@@ -280,7 +280,12 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
                     xr[k][a] = make_float2(v, v);
                 }
         }
-        const float *cscale = s_cscale + c0;
+        // column scales: registers for 16 columns (4 per thread), shared memory for 48
+        float cs_reg[SN == 16 ? CPT : 1];
+        if (SN == 16)
+#pragma unroll
+            for (int q = 0; q < (SN == 16 ? CPT : 1); ++q) cs_reg[q] = s_cscale[c0 + q];
+        auto cscale_of = [&](int q) -> float { return SN == 16 ? cs_reg[q] : s_cscale[c0 + q]; };
         float acc[CPT];
 #pragma unroll
         for (int q = 0; q < CPT; ++q) acc[q] = 0.f;
@@ -288,9 +293,14 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
         // Waits of the eval threads never leave the loop: after the first timeout (error
         // word set) every later wait is skipped and nothing more is added to W, so all
         // threads finish quickly.
+        // (the shared error word is read once per block into err_seen)
+        bool err_seen = false;
         auto wait_ok = [&](uint64_t *bar, uint32_t parity) {
-            if (*reinterpret_cast<volatile int *>(s_err)) return;
-            if (!mbar_wait(bar, parity)) atomicOr(s_err, ERR_TIMEOUT);
+            if (err_seen) return;
+            if (!mbar_wait(bar, parity)) {
+                atomicOr(s_err, ERR_TIMEOUT);
+                err_seen = true;
+            }
         };
         // D chunk k -> fp32 partial sums in registers
         auto drain_d = [&](int k) {
@@ -340,12 +350,12 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
             int J = I + bb;
             if (J >= NB) J -= NB;
             const int64_t r0 = (int64_t)J * BR;
-            if (r0 + row < p.n && !*reinterpret_cast<volatile int *>(s_err)) {
+            if (r0 + row < p.n && !err_seen) {
                 float val[CPT];
 #pragma unroll
                 for (int q = 0; q < CPT; ++q)
                     val[q] = (NPROD == 3 ? __uint_as_float(tr[q]) + __uint_as_float(tl[q]) : __uint_as_float(tr[q])) *
-                             cscale[q];
+                             cscale_of(q);
                 add_row(r0 + row, val);
             }
         };
@@ -354,6 +364,7 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
         int drained = 0;
         for (int b = 0; b < T; ++b) {
             const int s = b % SL, sa = b & 1;
+            err_seen = err_seen || *reinterpret_cast<volatile int *>(s_err) != 0;
             if (DRAIN && b % SKCH == SKCH / 2 && b >= SKCH + SKCH / 2) drain_d(drained++);
             if (b >= 3) {
                 drain_t_issue(b - 2);
@@ -404,6 +415,7 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
             mbar_arrive(&afull[sa]);
         }
         // ---------------- tail: remaining transposed blocks, D chunks, own rows
+        err_seen = err_seen || *reinterpret_cast<volatile int *>(s_err) != 0;
         wait_ok(done, 0);
         tc_fence_after();
         for (int bb = std::max(1, T - 2); bb < T; ++bb) {
@@ -427,12 +439,12 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
                 for (int q = 0; q < CPT; ++q) v[q] = __uint_as_float(h[q]);
             }
             const int64_t r0 = (int64_t)I * BR;
-            if (r0 + row < p.n && !*reinterpret_cast<volatile int *>(s_err)) {
+            if (r0 + row < p.n && !err_seen && !*reinterpret_cast<volatile int *>(s_err)) {
                 float outv[CPT];
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
                     const int col = c0 + q;
-                    outv[q] = col < p.c ? v[q] * cscale[q] + p.noise * p.V[(r0 + row) * p.c + col] : 0.f;
+                    outv[q] = col < p.c ? v[q] * cscale_of(q) + p.noise * p.V[(r0 + row) * p.c + col] : 0.f;
                 }
                 add_row(r0 + row, outv);
             }
