@@ -76,6 +76,131 @@ __global__ void __launch_bounds__(NT) gemm_nn_kernel(int64_t m, int q, int k, T 
     }
 }
 
+// Skinny forms for q <= 64 (the preconditioner applies of the CG, 16 or 48 columns):
+// 256 x 16 tiles (4 x 4 per thread, 64 row groups x 4 column groups), one column tile
+// of 16 per grid row, so no thread computes padding columns.
+constexpr int SBM = 256, SBN = 16;
+
+// C(m x q) = alpha A(m x k) B(k x q) + beta C, skinny tile.
+template <typename T>
+__global__ void __launch_bounds__(NT) gemm_nn_skinny_kernel(int64_t m, int q, int k, T alpha,
+                                                            const T *__restrict__ A, int64_t lda,
+                                                            const T *__restrict__ B, int64_t ldb, T beta,
+                                                            T *__restrict__ C, int64_t ldc) {
+    __shared__ T As[BK][SBM + 1];
+    __shared__ T Bs[BK][SBN];
+    const int tid = threadIdx.x;
+    const int tx = tid % 4, ty = tid / 4;
+    const int64_t row0 = (int64_t)blockIdx.x * SBM;
+    const int col0 = blockIdx.y * SBN;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int k0 = 0; k0 < k; k0 += BK) {
+#pragma unroll
+        for (int l = 0; l < (SBM * BK) / NT; ++l) {
+            const int e = tid + l * NT;
+            const int mm = e / BK, kk = e % BK;
+            const int64_t gr = row0 + mm;
+            const int gk = k0 + kk;
+            As[kk][mm] = (gr < m && gk < k) ? A[gr * lda + gk] : T(0);
+        }
+        {
+            const int kk = tid / SBN, nn = tid % SBN;
+            const int gk = k0 + kk, gc = col0 + nn;
+            Bs[kk][nn] = (gk < k && gc < q) ? B[(int64_t)gk * ldb + gc] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t gr = row0 + ty * 4 + a;
+        if (gr >= m) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int gc = col0 + tx * 4 + b;
+            if (gc >= q) continue;
+            T v = alpha * acc[a][b];
+            if (beta != T(0)) v += beta * C[gr * ldc + gc];
+            C[gr * ldc + gc] = v;
+        }
+    }
+}
+
+// partial[split](p x q) = A[rows of split]^T B[rows of split], skinny tile (p in 256s, q in 16s).
+template <typename T>
+__global__ void __launch_bounds__(NT) gemm_tn_skinny_kernel(int64_t m, int p, int q, int64_t rows_per,
+                                                            const T *__restrict__ A, int64_t lda,
+                                                            const T *__restrict__ B, int64_t ldb,
+                                                            double *__restrict__ part) {
+    __shared__ T As[BK][SBM];
+    __shared__ T Bs[BK][SBN];
+    const int tid = threadIdx.x;
+    const int tx = tid % 4, ty = tid / 4;
+    const int p0 = blockIdx.x * SBM, q0 = blockIdx.y * SBN;
+    const int64_t r0 = (int64_t)blockIdx.z * rows_per;
+    const int64_t r1 = min(m, r0 + rows_per);
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int64_t k0 = r0; k0 < r1; k0 += BK) {
+#pragma unroll
+        for (int l = 0; l < (SBM * BK) / NT; ++l) {
+            const int e = tid + l * NT;
+            const int kk = e / SBM, pp = e % SBM;
+            const int64_t gr = k0 + kk;
+            As[kk][pp] = (gr < r1 && p0 + pp < p) ? A[gr * lda + p0 + pp] : T(0);
+        }
+        {
+            const int kk = tid / SBN, nn = tid % SBN;
+            const int64_t gr = k0 + kk;
+            Bs[kk][nn] = (gr < r1 && q0 + nn < q) ? B[gr * ldb + q0 + nn] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        }
+        __syncthreads();
+    }
+    double *out = part + (size_t)blockIdx.z * p * q;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int gp = p0 + ty * 4 + a;
+        if (gp >= p) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int gq = q0 + tx * 4 + b;
+            if (gq < q) out[(size_t)gp * q + gq] = (double)acc[a][b];
+        }
+    }
+}
+
 // partial[split](p x q) = A[rows of split]^T B[rows of split]
 template <typename T>
 __global__ void __launch_bounds__(NT) gemm_tn_kernel(int64_t m, int p, int q, int64_t rows_per,
@@ -258,6 +383,11 @@ template <typename T>
 int gemm_nn(int64_t m, int q, int k, T alpha, const T *A, int64_t lda, const T *B, int64_t ldb,
             T beta, T *C, int64_t ldc, cudaStream_t st) {
     if (m == 0 || q == 0) return LD_OK;
+    if (q <= 64) {
+        dim3 grid((unsigned)((m + SBM - 1) / SBM), (unsigned)((q + SBN - 1) / SBN));
+        gemm_nn_skinny_kernel<T><<<grid, NT, 0, st>>>(m, q, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        return check_launch("gemm_nn");
+    }
     dim3 grid((unsigned)((m + BM - 1) / BM), (unsigned)((q + BN - 1) / BN));
     gemm_nn_kernel<T><<<grid, NT, 0, st>>>(m, q, k, alpha, A, lda, B, ldb, beta, C, ldc);
     return check_launch("gemm_nn");
@@ -275,8 +405,13 @@ int gemm_tn(int64_t m, int p, int q, const T *A, int64_t lda, const T *B, int64_
     int64_t rows_per = (m + ns - 1) / ns;
     rows_per = ((rows_per + BK - 1) / BK) * BK;
     if (rows_per == 0) rows_per = BK;
-    dim3 grid((unsigned)((p + BM - 1) / BM), (unsigned)((q + BN - 1) / BN), (unsigned)ns);
-    gemm_tn_kernel<T><<<grid, NT, 0, st>>>(m, p, q, rows_per, A, lda, B, ldb, part);
+    if (q <= 64) {
+        dim3 grid((unsigned)((p + SBM - 1) / SBM), (unsigned)((q + SBN - 1) / SBN), (unsigned)ns);
+        gemm_tn_skinny_kernel<T><<<grid, NT, 0, st>>>(m, p, q, rows_per, A, lda, B, ldb, part);
+    } else {
+        dim3 grid((unsigned)((p + BM - 1) / BM), (unsigned)((q + BN - 1) / BN), (unsigned)ns);
+        gemm_tn_kernel<T><<<grid, NT, 0, st>>>(m, p, q, rows_per, A, lda, B, ldb, part);
+    }
     LD_TRY(check_launch("gemm_tn"));
     int64_t count = (int64_t)p * q;
     reduce_splits_kernel<<<blocks_for(count), 256, 0, st>>>(part, ns, count, Cd);
