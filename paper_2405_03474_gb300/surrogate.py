@@ -4,7 +4,8 @@ An addition to the paper's method for hyperparameter search: the MLP of
 ``csrc/mlp.cu`` maps (log lengthscale, log variance, log noise, log n) to
 log det M / n.  Labels come from ``logdet_estimate`` (r_3, randomized-SVD
 preconditioner) on the GPU; the estimator stays the fallback (queries outside
-the training box) and the judge (audits on random queries).
+the training box) and the reference its error is measured against (audits on
+random queries).
 
 Run ``python -m paper_2405_03474_gb300.surrogate --help`` for the label job of the
 ``surrogate_matern_n262144_d3`` workload (checkpointed to an .npz, resumable).
@@ -81,7 +82,7 @@ def generate_labels(est, thetas, checkpoint=None, every=32, log=None):
 
 
 class HyperSurrogate:
-    """Trained network plus the estimator as fallback and judge."""
+    """Trained network plus the estimator as fallback and as the reference of its error."""
 
     def __init__(self, est, box=inputs.THETA_BOX, seed=0):
         self.est = est
