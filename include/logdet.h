@@ -139,7 +139,13 @@ int ld_rk_coeffs(int32_t order, double *b, double *c, double *sigma);
  * spends its O(t n^2) time in (Section 2, complexity paragraph).
  * X_dev: n-by-d float64.  V_dev, W_dev: n-by-c row-major, float64 for
  * LD_FP64, float32 otherwise (W_dev must not alias V_dev).  No workspace for
- * FP64/FP32; TC modes need ld_kz_workspace_size(n, d, c, precision) bytes. */
+ * FP64/FP32; TC modes need ld_kz_workspace_size(n, d, c, precision) bytes.
+ * Sizes: n >= 1, 1 <= c <= 4096, 1 <= d <= 32 (d <= 8 in the tensor-core
+ * precisions); anything else, empty inputs included, returns LD_ERR_INVALID
+ * before any device work.  ws = NULL: the call allocates and frees its own
+ * workspace.  Tensor-core dispatch (all within the call): c <= 48 and n >= 256
+ * the symmetric product, 256 < c <= 512 in fp16/bf16 the one-pass wide
+ * product, otherwise the general product in chunks of 256 columns. */
 size_t ld_kz_workspace_size(int64_t n, int32_t d, int32_t c, int32_t precision);
 int ld_kz(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
           const void *V_dev, void *W_dev, int32_t c, int32_t precision,
