@@ -487,6 +487,7 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
             LD_TRY(check_launch("cg_init"));
             int it = 0;
             for (; it < max_iters; ++it) {
+                NvtxRange range("ld: CG iteration");
                 // Bp = (B + sigma_min I) p   (the O(n^2) step)
                 LD_TRY(apply_B<T>(P, b, b.Xs, n, d, kern, b.p, b.Bp, b.y, b.w, s, smin, o.precision, a, st));
                 LD_TRY(coldot<T>(n, s, b.p, b.Bp, b.dots, b.part, st));
@@ -532,6 +533,7 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
             interleave_kernel<T><<<nb(nsm), 256, 0, st>>>(n, s, m, b.xs, b.Xall);
             LD_TRY(check_launch("interleave"));
             if (o.residual_check) {
+                NvtxRange range("ld: residual check");
                 // ||z - (B + sigma_j) x_j|| / ||z||, one extra pass over all s*m columns
                 LD_TRY(apply_B<T>(P, b, b.Xs, n, d, kern, b.Xall, b.W1, b.Y, b.W2, sm, 0.0, o.precision, a, st));
                 residual_kernel<T><<<nb(nsm), 256, 0, st>>>(n, s, m, b.Z, b.Xall, b.W1, rk);
@@ -545,6 +547,7 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
                         out.max_resid[j] = std::max(out.max_resid[j], sqrt(rn[c * m + j] / cs[c].znorm2));
             }
             if (want_grad) {
+                NvtxRange range("ld: adjoint");
                 // y = L^-T x;  dest/dtheta = (1/s) sum (-c_j) y^T dM y
                 if (P) {
                     LD_TRY(precond_apply_impl<T>(P, true, b.Xall, b.Y, sm, b.Td, b.Tt, b.Ut, b.ppart, st));

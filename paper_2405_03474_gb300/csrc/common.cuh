@@ -8,9 +8,21 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "logdet.h"
 
 namespace ld {
+
+// Scoped NVTX range around a phase (preconditioner build, sketch product, CG
+// iteration, residual pass, adjoint, kernel product): visible in Nsight timelines,
+// a no-op when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ------------------------------------------------------------ error state
 void set_error(const char *fmt, ...);

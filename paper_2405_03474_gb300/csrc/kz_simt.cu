@@ -159,12 +159,14 @@ size_t kz_any_workspace<float>(int64_t n, int d, int c, int precision) {
 template <>
 int kz_any<double>(const double *Xs, int64_t n, int d, const ld_kernel &k, const double *V, double *W,
                    int c, int precision, Arena &, cudaStream_t st) {
+    NvtxRange range("ld: kernel product");
     (void)precision;
     return kz_simt<double>(Xs, n, d, k.kind, k.variance, k.noise, V, W, c, st);
 }
 template <>
 int kz_any<float>(const float *Xs, int64_t n, int d, const ld_kernel &k, const float *V, float *W,
                   int c, int precision, Arena &ws, cudaStream_t st) {
+    NvtxRange range("ld: kernel product");
     if (precision == LD_FP32 || precision == LD_FP64)
         return kz_simt<float>(Xs, n, d, k.kind, k.variance, k.noise, V, W, c, st);
     return kz_tc(Xs, n, d, k.kind, k.variance, k.noise, V, W, c, precision, ws, st);

@@ -263,6 +263,7 @@ template <typename T>
 int build_impl(const double *X, int64_t n, int d, const ld_kernel &kern, int r, int q,
                uint64_t seed, int precision, double const_d, void *ws, size_t ws_bytes, cudaStream_t st,
                ld_precond **out) {
+    NvtxRange range("ld: preconditioner build");
     Arena a;
     size_t need = build_bytes<T>(n, d, r, precision);
     LD_TRY(arena_open(a, ws, ws_bytes, need));
