@@ -299,6 +299,13 @@ int ld_profile_kernel(int32_t kernel, double *ms, int64_t *launches, double *pai
 int surrogate_create(uint64_t seed, void *stream, ld_surrogate **out);
 int surrogate_set_params(ld_surrogate *S, const float *params_host, void *stream);
 int surrogate_get_params(const ld_surrogate *S, float *params_host, void *stream);
+/* The affine normalisation the handle applies (set by surrogate_train from its
+ * data): 10 floats, input means mu[4], input scales sd[4], target mean, target
+ * scale; with the parameters it is the whole state of a trained network (a
+ * checkpoint).  set: scales must be > 0 and every entry finite, else
+ * LD_ERR_INVALID. */
+int surrogate_get_norm(const ld_surrogate *S, float *norm_host, void *stream);
+int surrogate_set_norm(ld_surrogate *S, const float *norm_host, void *stream);
 /* One full-batch gradient: loss and d loss / d params for (theta_dev N-by-4,
  * y_dev N), written to grad_host (33793) if not NULL. */
 int surrogate_loss_grad(ld_surrogate *S, const float *theta_dev, const float *y_dev,

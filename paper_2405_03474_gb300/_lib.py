@@ -96,6 +96,8 @@ _SIGS = {
     "surrogate_create": (c_int32, [c_uint64, _P, _P]),
     "surrogate_set_params": (c_int32, [_P, _P, _P]),
     "surrogate_get_params": (c_int32, [_P, _P, _P]),
+    "surrogate_get_norm": (c_int32, [_P, _P, _P]),
+    "surrogate_set_norm": (c_int32, [_P, _P, _P]),
     "surrogate_loss_grad": (c_int32, [_P, _P, _P, c_int32, _P, _P, _P]),
     "surrogate_train": (c_int32, [_P, _P, _P, c_int32, c_int32, c_int32, c_float, _P, _P]),
     "surrogate_infer": (c_int32, [_P, _P, c_int32, _P, _P, _P]),

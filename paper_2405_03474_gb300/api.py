@@ -320,6 +320,28 @@ class Surrogate:
               "surrogate_get_params")
         return flat
 
+    def get_norm(self, stream=None):
+        norm = np.zeros(10, dtype=np.float32)
+        check(_lib.load().surrogate_get_norm(self._h, norm.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+              "surrogate_get_norm")
+        return norm
+
+    def set_norm(self, norm, stream=None):
+        norm = np.ascontiguousarray(norm, dtype=np.float32)
+        assert norm.size == 10
+        check(_lib.load().surrogate_set_norm(self._h, norm.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+              "surrogate_set_norm")
+
+    def save(self, path):
+        """Checkpoint: parameters and normalisation to an .npz file."""
+        np.savez(path, params=self.get_params(), norm=self.get_norm())
+
+    def load(self, path):
+        """Restore a checkpoint written by save()."""
+        with np.load(path) as z:
+            self.set_params(z["params"])
+            self.set_norm(z["norm"])
+
     @staticmethod
     def _f32(t, cols):
         _need_cuda(t)

@@ -346,6 +346,31 @@ int surrogate_get_params(const ld_surrogate *S, float *params_host, void *stream
     return LD_OK;
 }
 
+int surrogate_get_norm(const ld_surrogate *S, float *norm_host, void *stream) {
+    ld::clear_error();
+    LD_TRY(check_handle(S));
+    LD_REQUIRE(norm_host != nullptr, "surrogate_get_norm: NULL norm");
+    cudaStream_t st = (cudaStream_t)stream;
+    LD_CHECK_CUDA(cudaMemcpyAsync(norm_host, S->norm, 10 * sizeof(float), cudaMemcpyDeviceToHost, st));
+    LD_CHECK_CUDA(cudaStreamSynchronize(st));
+    return LD_OK;
+}
+
+int surrogate_set_norm(ld_surrogate *S, const float *norm_host, void *stream) {
+    ld::clear_error();
+    LD_TRY(check_handle(S));
+    LD_REQUIRE(norm_host != nullptr, "surrogate_set_norm: NULL norm");
+    for (int k = 0; k < 10; ++k) {
+        const bool scale = (k >= 4 && k < 8) || k == 9;  // sd[4] and ysd
+        LD_REQUIRE(isfinite(norm_host[k]) && (!scale || norm_host[k] > 0.f),
+                   "surrogate_set_norm: entry %d must be finite (and > 0 for a scale)", k);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    LD_CHECK_CUDA(cudaMemcpyAsync(S->norm, norm_host, 10 * sizeof(float), cudaMemcpyHostToDevice, st));
+    LD_CHECK_CUDA(cudaStreamSynchronize(st));
+    return LD_OK;
+}
+
 int surrogate_loss_grad(ld_surrogate *S, const float *theta_dev, const float *y_dev, int32_t N,
                         double *loss_host, float *grad_host, void *stream) {
     ld::clear_error();

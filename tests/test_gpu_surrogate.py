@@ -104,3 +104,21 @@ def test_surrogate_gain_over_the_estimator():
     # (the symmetric kernel product adds the blocks of different CTAs in arrival order,
     # so two estimates of one theta agree to fp32 rounding of the sums, not bit for bit)
     assert out[0] and p[0] == pytest.approx(est(far[0]), rel=1e-6)
+
+
+def test_checkpoint_round_trip(tmp_path):
+    # a trained network saved (parameters + normalisation) and restored into a fresh handle
+    # predicts bit for bit what the original predicts
+    rng = np.random.default_rng(4)
+    theta = rng.uniform(-1, 1, size=(512, 4)).astype(np.float32)
+    y = (np.sin(theta[:, 0]) + theta[:, 1] * theta[:, 2] + 3.0).astype(np.float32)
+    net = api.Surrogate(seed=5)
+    net.train(cuda(theta), cuda(y), epochs=20, batch=64, lr=2e-3)
+    q = cuda(rng.uniform(-1, 1, size=(300, 4)).astype(np.float32))
+    ref = host(net.infer(q))
+    path = str(tmp_path / "surrogate.npz")
+    net.save(path)
+    other = api.Surrogate(seed=99)
+    other.load(path)
+    np.testing.assert_array_equal(host(other.infer(q)), ref)
+    np.testing.assert_array_equal(other.get_norm(), net.get_norm())
