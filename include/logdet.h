@@ -247,7 +247,9 @@ void precond_free(ld_precond *P);
  * P = NULL means P = I.  probes_dev: n-by-num_probes int8 (+-1), or NULL to
  * draw them with ld_rademacher(opt->seed, ...).  per_probe_host: optional
  * (num_probes doubles) receives the bracket per probe.
- * Returns LD_ERR_NOT_CONVERGED (with *out filled) when rel_tol was not met. */
+ * Returns LD_ERR_NOT_CONVERGED (with *out filled) when rel_tol was not met, and
+ * LD_ERR_NOT_SPD (with *out filled) when the estimate is not finite (non-finite
+ * points or parameters, or a matrix that is not SPD). */
 size_t logdet_workspace_size(int64_t n, int32_t d, const ld_precond *P,
                              const ld_options *opt);
 int logdet_estimate(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,

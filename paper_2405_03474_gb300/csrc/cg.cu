@@ -674,6 +674,12 @@ int logdet_estimate(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, c
                    : run_impl<float>(X_dev, n, d, kern, P, *opt, probes_dev, ws, ws_bytes, st, false, r);
     if (code != LD_OK) return code;
     fill_result(r, P, *opt, out, per_probe_host);
+    if (!isfinite(out->logdet)) {
+        // NaN / Inf guard: a non-finite point or parameter, or an operator that is not SPD
+        set_error("non-finite estimate (logdet_P %g, trace %g): the points or kernel parameters do not give a "
+                  "finite SPD matrix", out->logdet_P, out->trace_est);
+        return LD_ERR_NOT_SPD;
+    }
     if (!r.converged) {
         set_error("CG did not reach rel_tol %.3g in %d iterations (final %.3g)", opt->rel_tol,
                   opt->max_iters, r.final_rel);
@@ -696,6 +702,11 @@ int logdet_grad(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, const
     if (code != LD_OK) return code;
     fill_result(r, P, *opt, out, nullptr);
     for (int a = 0; a < 3; ++a) grad_host[a] = r.grad[a];
+    if (!isfinite(out->logdet) || !isfinite(r.grad[0]) || !isfinite(r.grad[1]) || !isfinite(r.grad[2])) {
+        set_error("non-finite estimate or gradient: the points or kernel parameters do not give a finite SPD "
+                  "matrix");
+        return LD_ERR_NOT_SPD;
+    }
     if (!r.converged) {
         set_error("CG did not reach rel_tol %.3g in %d iterations", opt->rel_tol, opt->max_iters);
         return LD_ERR_NOT_CONVERGED;

@@ -61,3 +61,13 @@ def test_workspace_too_small_is_refused():
                    ctypes.c_void_p(W.data_ptr()), c, api.PRECISIONS["f16x3_tc"], ctypes.c_void_p(ws.data_ptr()),
                    need // 2, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == _lib.LD_ERR_WORKSPACE
+
+
+def test_non_finite_input_is_reported_not_returned_as_a_number():
+    # a NaN coordinate gives NaN kernel values; the estimate's NaN/Inf guard reports it
+    X = inputs.points(300, 2, "uniform", seed=7)
+    X[5, 1] = np.nan
+    with pytest.raises(_lib.LogdetError) as e:
+        api.logdet_estimate(cuda(X), api.Kernel(api.RBF, 0.3, 1.0, 1e-2), order=3, num_probes=4,
+                            precision="fp64", fixed_iters=5, max_iters=5)
+    assert e.value.status == _lib.LD_ERR_NOT_SPD and "non-finite" in str(e.value)
