@@ -451,6 +451,7 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
             set_error("internal: estimator workspace overflow");
             return LD_ERR_WORKSPACE;
         }
+        LD_TRY(check_points_finite(X, n, d, b.n_active, st));
         LD_TRY(prep_points<T>(X, n, d, point_scale(kern), b.Xs, st));
         if (dense) LD_TRY(dense_materialize<T>(b.Xs, n, d, kern, b.M, st));
         const size_t ns = (size_t)n * s;

@@ -121,6 +121,9 @@ double point_scale(const ld_kernel &k);
 
 template <typename T>
 int prep_points(const double *X, int64_t n, int d, double scale, T *Xs, cudaStream_t st);
+// LD_ERR_INVALID if any of the n*d coordinates is NaN or Inf (flag_dev: one device
+// int of scratch; synchronises the stream)
+int check_points_finite(const double *X, int64_t n, int d, int *flag_dev, cudaStream_t st);
 
 // W = (K + noise I) V (SIMT), V, W n-by-c row-major
 template <typename T>

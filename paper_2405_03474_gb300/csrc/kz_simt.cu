@@ -25,6 +25,11 @@ __global__ void prep_points_kernel(const double *X, int64_t count, double scale,
     if (t < count) Xs[t] = (T)(X[t] * scale);
 }
 
+__global__ void finite_check_kernel(const double *X, int64_t count, int *flag) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < count && !isfinite(X[t])) atomicOr(flag, 1);
+}
+
 template <typename T, int KIND, int DC, bool DERIV>
 __global__ void __launch_bounds__(TPB) kz_simt_kernel(const T *__restrict__ Xs, int64_t n, int d,
                                                       const T *__restrict__ V, T *__restrict__ W,
@@ -112,6 +117,21 @@ int launch_kz(const T *Xs, int64_t n, int d, const T *V, T *W, T *Wdl, int c, T 
 }
 
 }  // namespace
+
+int check_points_finite(const double *X, int64_t n, int d, int *flag_dev, cudaStream_t st) {
+    const int64_t count = n * d;
+    LD_CHECK_CUDA(cudaMemsetAsync(flag_dev, 0, sizeof(int), st));
+    finite_check_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(X, count, flag_dev);
+    LD_TRY(check_launch("finite_check"));
+    int h = 0;
+    LD_CHECK_CUDA(cudaMemcpyAsync(&h, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LD_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        set_error("non-finite point coordinate (NaN or Inf) in X");
+        return LD_ERR_INVALID;
+    }
+    return LD_OK;
+}
 
 template <typename T>
 int prep_points(const double *X, int64_t n, int d, double scale, T *Xs, cudaStream_t st) {

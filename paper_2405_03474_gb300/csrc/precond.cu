@@ -287,6 +287,7 @@ int build_impl(const double *X, int64_t n, int d, const ld_kernel &kern, int r, 
                 return LD_ERR_WORKSPACE;
             }
             LD_CHECK_CUDA(cudaMemsetAsync(s.status, 0, 16 * sizeof(int), st));
+            LD_TRY(check_points_finite(X, n, d, s.status + 15, st));
             LD_TRY(prep_points<T>(X, n, d, point_scale(kern), Xs, st));
             const double diagM = kern.variance + kern.noise;
             const double floor = std::max(kern.noise, 1e-12 * diagM);

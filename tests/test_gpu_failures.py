@@ -63,11 +63,15 @@ def test_workspace_too_small_is_refused():
     assert st == _lib.LD_ERR_WORKSPACE
 
 
-def test_non_finite_input_is_reported_not_returned_as_a_number():
-    # a NaN coordinate gives NaN kernel values; the estimate's NaN/Inf guard reports it
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_non_finite_points_are_refused(bad):
+    # a NaN or Inf coordinate is reported by the estimator and the preconditioner build
     X = inputs.points(300, 2, "uniform", seed=7)
-    X[5, 1] = np.nan
+    X[5, 1] = bad
+    k = api.Kernel(api.RBF, 0.3, 1.0, 1e-2)
     with pytest.raises(_lib.LogdetError) as e:
-        api.logdet_estimate(cuda(X), api.Kernel(api.RBF, 0.3, 1.0, 1e-2), order=3, num_probes=4,
-                            precision="fp64", fixed_iters=5, max_iters=5)
-    assert e.value.status == _lib.LD_ERR_NOT_SPD and "non-finite" in str(e.value)
+        api.logdet_estimate(cuda(X), k, order=3, num_probes=4, precision="fp64", fixed_iters=5, max_iters=5)
+    assert e.value.status == _lib.LD_ERR_INVALID and "non-finite" in str(e.value)
+    with pytest.raises(_lib.LogdetError) as e:
+        api.Precond.build(cuda(X), k, 8, precision="fp64")
+    assert e.value.status == _lib.LD_ERR_INVALID and "non-finite" in str(e.value)
