@@ -208,7 +208,8 @@ int ld_rademacher(uint64_t seed, int64_t n, int32_t s, int32_t col0,
  * value keeps n-by-rank factors in float32, r-by-r factors in float64, and
  * runs the M products in that precision.
  * rank = 0 gives P = diag(M) (Appendix "Diagonal"); P = NULL in
- * logdet_estimate means P = I (Appendix "Identity"). */
+ * logdet_estimate means P = I (Appendix "Identity").  A NaN or Inf coordinate
+ * in X returns LD_ERR_INVALID; a Cholesky pivot <= 0 returns LD_ERR_NOT_SPD. */
 size_t precond_workspace_size(int64_t n, int32_t d, int32_t rank, int32_t precision);
 int precond_build(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
                   int32_t rank, int32_t power_iters, uint64_t seed,
@@ -247,9 +248,10 @@ void precond_free(ld_precond *P);
  * P = NULL means P = I.  probes_dev: n-by-num_probes int8 (+-1), or NULL to
  * draw them with ld_rademacher(opt->seed, ...).  per_probe_host: optional
  * (num_probes doubles) receives the bracket per probe.
- * Returns LD_ERR_NOT_CONVERGED (with *out filled) when rel_tol was not met, and
- * LD_ERR_NOT_SPD (with *out filled) when the estimate is not finite (non-finite
- * points or parameters, or a matrix that is not SPD). */
+ * Returns LD_ERR_INVALID for a NaN or Inf coordinate in X (checked on the
+ * device first), LD_ERR_NOT_CONVERGED (with *out filled) when rel_tol was not
+ * met, and LD_ERR_NOT_SPD (with *out filled) when the estimate is not finite
+ * (a matrix that is not SPD). */
 size_t logdet_workspace_size(int64_t n, int32_t d, const ld_precond *P,
                              const ld_options *opt);
 int logdet_estimate(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
