@@ -13,19 +13,24 @@ namespace {
 
 constexpr int CHOL_THREADS = 1024;
 
-// Right-looking Cholesky, one CTA.  A is r x r row-major; the lower triangle is
-// read and overwritten by L, the strict upper triangle is zeroed.
+// Right-looking Cholesky, one CTA of 32 x 32 threads.  A is r x r row-major; the
+// lower triangle is read and overwritten by L, the strict upper triangle is
+// zeroed.  Column k of L (below the diagonal) is kept in shared memory for the
+// rank-1 update of the trailing lower triangle, whose rows go to the 32 thread
+// rows and whose columns to the 32 lanes (coalesced, no index division).
 __global__ void __launch_bounds__(CHOL_THREADS) chol_kernel(double *A, int r, double shift,
                                                             int *status) {
+    extern __shared__ double s_col[];  // r: column k of L
     __shared__ double s_piv;
     __shared__ int s_bad;
     const int tid = threadIdx.x;
+    const int tx = tid & 31, ty = tid >> 5;
     if (tid == 0) s_bad = 0;
     for (int i = tid; i < r; i += CHOL_THREADS) A[(size_t)i * r + i] += shift;
     __syncthreads();
     for (int k = 0; k < r; ++k) {
         if (tid == 0) {
-            double akk = A[(size_t)k * r + k];
+            const double akk = A[(size_t)k * r + k];
             if (!(akk > 0.0)) {
                 s_bad = k + 1;
                 s_piv = 1.0;
@@ -37,21 +42,22 @@ __global__ void __launch_bounds__(CHOL_THREADS) chol_kernel(double *A, int r, do
         __syncthreads();
         if (s_bad) break;
         const double piv = s_piv;
-        for (int i = k + 1 + tid; i < r; i += CHOL_THREADS) A[(size_t)i * r + k] /= piv;
+        for (int i = k + 1 + tid; i < r; i += CHOL_THREADS) {
+            const double v = A[(size_t)i * r + k] / piv;
+            A[(size_t)i * r + k] = v;
+            s_col[i] = v;
+        }
         __syncthreads();
-        const int m = r - k - 1;  // trailing block size
-        const int64_t sq = (int64_t)m * m;
-        for (int64_t e = tid; e < sq; e += CHOL_THREADS) {
-            int ii = (int)(e / m), jj = (int)(e % m);
-            if (jj > ii) continue;
-            int i = k + 1 + ii, j = k + 1 + jj;
-            A[(size_t)i * r + j] -= A[(size_t)i * r + k] * A[(size_t)j * r + k];
+        for (int i = k + 1 + ty; i < r; i += 32) {
+            const double li = s_col[i];
+            double *row = A + (size_t)i * r;
+            for (int j = k + 1 + tx; j <= i; j += 32) row[j] -= li * s_col[j];
         }
         __syncthreads();
     }
     __syncthreads();
     for (int64_t e = tid; e < (int64_t)r * r; e += CHOL_THREADS) {
-        int i = (int)(e / r), j = (int)(e % r);
+        const int i = (int)(e / r), j = (int)(e % r);
         if (j > i) A[e] = 0.0;
     }
     if (tid == 0) *status = s_bad;
@@ -151,7 +157,7 @@ __global__ void export_kernel(const double *src, T *dst, int r, double add, bool
 
 int dense_chol(double *A, int r, double shift, int *status, cudaStream_t st) {
     if (r == 0) return LD_OK;
-    chol_kernel<<<1, CHOL_THREADS, 0, st>>>(A, r, shift, status);
+    chol_kernel<<<1, CHOL_THREADS, r * sizeof(double), st>>>(A, r, shift, status);
     return check_launch("dense_chol");
 }
 
