@@ -75,9 +75,13 @@ def gaussian(n, s, seed):
 
 def sobol_theta(count, seed=0, box=THETA_BOX):
     """count-by-3 hyperparameters (l, v, nu), scrambled Sobol in log space."""
+    import warnings
+
     from scipy.stats import qmc
 
-    u = qmc.Sobol(d=3, scramble=True, seed=seed).random(count)
+    with warnings.catch_warnings():  # counts that are not powers of two are intended here
+        warnings.simplefilter("ignore", UserWarning)
+        u = qmc.Sobol(d=3, scramble=True, seed=seed).random(count)
     lo = np.log([box["lengthscale"][0], box["variance"][0], box["noise"][0]])
     hi = np.log([box["lengthscale"][1], box["variance"][1], box["noise"][1]])
     return np.exp(lo + u * (hi - lo))
