@@ -92,7 +92,9 @@ typedef struct {
     int32_t precision;       /* ld_precision */
     int32_t residual_check;  /* 1: fill ld_result.max_resid (one extra K V pass) */
     int32_t dense;           /* 1: materialise M = K + noise I once (n*n words in the
-                                workspace) and apply it from HBM; 0: matrix-free */
+                                workspace) and apply it from HBM (tensor-core
+                                precisions: the dense tcgen05 product of
+                                ld_dense_kz); 0: matrix-free */
     uint64_t seed;           /* SplitMix64 seed of the probes when probes_dev is NULL */
     double rel_tol;          /* stop when max_i ||r_i|| / ||z_i|| < rel_tol (seed system) */
     int32_t probe_kind;      /* 0: Rademacher (Section 3); 1: N(0, 1) by Box-Muller from the
@@ -174,9 +176,18 @@ int ld_kz_dl(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
              const void *V_dev, void *W_dev, void *Wdl_dev, int32_t c,
              int32_t precision, void *stream);
 
-/* Stored dense variant of the same product: M = K + noise I written row-major
- * n-by-n (float64 for LD_FP64, float32 otherwise; ld_dense_bytes(n, precision)
- * bytes, caller-owned), then W = M V reading M once per product. */
+/* Stored dense variant of the same product (Algorithm 1 step 2 with M kept in
+ * memory): M = K + noise I written row-major n-by-n (float64 for LD_FP64, float32
+ * otherwise; ld_dense_bytes(n, precision) bytes, caller-owned), then W = M V
+ * (V, W n-by-c row-major, float64 for LD_FP64, else float32) reading M once per
+ * product.  LD_FP64 / LD_FP32: CUDA-core GEMM, asynchronous on the stream.
+ * Tensor-core precisions (LD_BF16_TC, LD_F16_TC, LD_F16X3_TC; c <= 4096): M is
+ * rounded (or split hi/lo) like the computed kernel values of ld_kz after
+ * scaling by the power of two that brings max_i |M_ii| below 1, so M must be
+ * positive semidefinite (|M_ij| <= max_i M_ii, true of every K + noise I; an
+ * entry beyond that may overflow fp16 and make W non-finite); the call
+ * allocates its scratch (the fp16/bf16 image of V), synchronises the stream and
+ * returns LD_ERR_DEVICE_TIMEOUT if a device-side wait gave up. */
 size_t ld_dense_bytes(int64_t n, int32_t precision);
 int ld_dense_materialize(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
                          int32_t precision, void *M_dev, void *stream);

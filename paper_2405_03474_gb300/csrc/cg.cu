@@ -16,6 +16,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -396,7 +397,10 @@ size_t run_bytes(int64_t n, int d, const ld_precond *P, int s, int m, int max_it
     // the free tail serves the kernel product and, before the CG starts, the
     // orthogonal-probe cores
     size_t tail = orth_probe_tail_bytes(n, s);
-    if (!dense) tail = std::max(tail, kz_any_workspace<T>(n, d, extra ? std::max(s, s * m) : s, precision));
+    const int cw = extra ? std::max(s, s * m) : s;
+    if (!dense) tail = std::max(tail, kz_any_workspace<T>(n, d, cw, precision));
+    else if (std::is_same<T, float>::value && is_tc_precision(precision))
+        tail = std::max(tail, dense_tc_workspace(n, cw, precision));
     meas.take<char>(tail);
     return meas.off;
 }
@@ -407,7 +411,12 @@ int apply_B(const ld_precond *P, Bufs<T> &b, const T *Xs, int64_t n, int d, cons
             const T *V, T *out, T *tmp1, T *tmp2, int c, double shift, int precision, Arena &a,
             cudaStream_t st) {
     auto product = [&](const T *in, T *o) -> int {
-        if (b.M) return dense_product<T>(b.M, n, in, o, c, st);
+        if (b.M) {
+            if constexpr (std::is_same<T, float>::value) {
+                if (is_tc_precision(precision)) return dense_tc(b.M, n, in, o, c, precision, a, st);
+            }
+            return dense_product<T>(b.M, n, in, o, c, st);
+        }
         return kz_any<T>(Xs, n, d, k, in, o, c, precision, a, st);
     };
     if (P) {

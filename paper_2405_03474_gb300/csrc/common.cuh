@@ -141,7 +141,15 @@ template <typename T>
 int dense_product(const T *M, int64_t n, const T *V, T *W, int c, cudaStream_t st);
 
 // tensor-core product (float vectors)
+inline bool is_tc_precision(int precision) {
+    return precision == LD_BF16_TC || precision == LD_F16_TC || precision == LD_F16X3_TC;
+}
 size_t kz_tc_workspace(int64_t n, int d, int c, int precision);
+// W = M V on the tensor cores for a stored dense M (row-major n x n float32, positive
+// semidefinite: it is scaled by a power of two taken from its diagonal), kz_tc.cu
+size_t dense_tc_workspace(int64_t n, int c, int precision);
+int dense_tc(const float *M, int64_t n, const float *V, float *W, int c, int precision, Arena &ws,
+             cudaStream_t st);
 // symmetric tensor-core product for c <= 16 (each kernel value evaluated once)
 // the one-pass product for 256 < c <= 512 columns, single fp16 / bf16 product (kz_wide.cu)
 bool kz_wide_eligible(int64_t n, int d, int c, int precision);

@@ -1,6 +1,8 @@
 // Stored dense M = K + noise I and its product W = M V: the variant of the
 // O(n^2) step (Algorithm 1 step 2) that keeps M in HBM and reads it once per
 // product, against evaluating K again in every pass (kz_simt.cu, kz_tc.cu).
+// FP64 and FP32 products run on the CUDA cores (gemm_nn); the tensor-core
+// precisions stream M through the tcgen05 pipeline of kz_tc.cu (dense_tc).
 #include "common.cuh"
 #include "kernel_fn.cuh"
 
@@ -124,10 +126,25 @@ int ld_dense_kz(const void *M_dev, int64_t n, const void *V_dev, void *W_dev, in
     clear_error();
     LD_REQUIRE(M_dev && V_dev && W_dev && n > 0 && c > 0 && V_dev != W_dev, "ld_dense_kz: bad arguments");
     LD_REQUIRE(n <= (int64_t)1 << 31, "ld_dense_kz: n too large");
+    LD_REQUIRE(precision >= LD_FP64 && precision <= LD_F16X3_TC, "ld_dense_kz: bad precision");
+    LD_REQUIRE(!is_tc_precision(precision) || c <= 4096, "ld_dense_kz: at most 4096 columns");
     cudaStream_t st = (cudaStream_t)stream;
     if (precision == LD_FP64)
         return dense_product<double>((const double *)M_dev, n, (const double *)V_dev, (double *)W_dev, c, st);
-    return dense_product<float>((const float *)M_dev, n, (const float *)V_dev, (float *)W_dev, c, st);
+    if (!is_tc_precision(precision))
+        return dense_product<float>((const float *)M_dev, n, (const float *)V_dev, (float *)W_dev, c, st);
+    // tensor cores: scratch for the operand image of V, allocated here and freed after the
+    // product (the call synchronises the stream)
+    Arena a;
+    LD_TRY(arena_open(a, nullptr, 0, dense_tc_workspace(n, c, precision)));
+    int code = dense_tc((const float *)M_dev, n, (const float *)V_dev, (float *)W_dev, c, precision, a, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (code == LD_OK && e != cudaSuccess) {
+        set_error("ld_dense_kz: %s", cudaGetErrorString(e));
+        code = LD_ERR_CUDA;
+    }
+    arena_close(a);
+    return code;
 }
 
 }  // extern "C"

@@ -22,6 +22,13 @@
 // (K = Kh + Kl, V = Vh + Vl in fp16; D += Kh Vh + Kh Vl + Kl Vh).  V columns are
 // scaled by powers of two so |V| <= 1 before rounding; K is computed with unit
 // variance and the variance is applied in the epilogue.
+//
+// The same pipeline serves a stored dense M = K + noise I (FROMM): the eval warps
+// then read their 4 rows x 8 columns of each 128 x 64 tile of M from HBM (streaming
+// loads, three tiles in flight per thread), scale them by a power of two that
+// brings max |M_ii| below 1 and round/split them exactly as computed values; the
+// producer streams only the operand image of V.  One pass reads M once, so the
+// product is bound by HBM instead of the FP32 pipes of the SIMT GEMM.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -57,6 +64,9 @@ struct TcParams {
     int ntiles;             // ceil(n / 64)
     float variance, noise;
     int *err;
+    const float *M;         // stored dense M (FROMM), row-major n x n
+    const float *mscale;    // FROMM: [0] power-of-two scale of M, [1] its inverse
+    int vec4;               // FROMM: n % 4 == 0 and M 16-byte aligned (float4 loads)
 };
 
 // Dynamic shared memory (from a 1024-aligned base):
@@ -84,8 +94,8 @@ __host__ __device__ inline Layout make_layout(int N, int d, int nprod, int sl) {
     return L;
 }
 
-template <int KIND, int DC, int NPROD, bool BF16, bool DRAIN>
-__global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L) {
+template <int KIND, int DC, int NPROD, bool BF16, bool DRAIN, bool FROMM>
+__global__ void __launch_bounds__(NTHREADS, FROMM ? 1 : 2) kz_tc_kernel(TcParams p, Layout L) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte aligned base by pointer arithmetic on the shared array itself, so the
     // compiler keeps shared-window loads and stores (an integer round trip would
@@ -146,7 +156,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
     if (warp == NEVAL + 1) {
         // ---------------- producer: point tile and operand image of V per j-tile
         if (lane == 0) {
-            const uint32_t xb = (uint32_t)(TJ * dd * 4);
+            const uint32_t xb = FROMM ? 0u : (uint32_t)(TJ * dd * 4);
             const uint32_t bb = (uint32_t)L.b_bytes;
             int t = 0;
             for (; t < T; ++t) {
@@ -158,7 +168,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
                 uint8_t *st = lbase + (size_t)s * L.l_bytes;
                 mbar_expect_tx(&full[s], xb + bb);
                 bulk_g2s(st, p.img + (size_t)t * bb, bb, &full[s]);
-                bulk_g2s(st + L.b_bytes, p.Xp + (size_t)t * TJ * dd, xb, &full[s]);
+                if (!FROMM) bulk_g2s(st + L.b_bytes, p.Xp + (size_t)t * TJ * dd, xb, &full[s]);
             }
             // every issued copy must land before the CTA may exit
             for (int u = std::max(0, t - SL); u < t; ++u) {
@@ -220,6 +230,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
         float2 xr[4][8];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
+            if (FROMM) break;
             const int r = rg + 32 * k;
             const float *tile = p.Xp + (size_t)(2 * blockIdx.x + (r >> 6)) * TJ * dd;
 #pragma unroll
@@ -246,7 +257,90 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
         const int C = (T + KCH - 1) / KCH;  // chunks
         int drained = 0;                     // chunks already drained
         bool ok = true;
-        for (int t = 0; t < T; ++t) {
+        if (FROMM) {
+            // stored M: rows rg + 32 k of the block, columns 8 kq .. 8 kq + 7 of each tile
+            const float ms = __ldg(p.mscale);
+            const float *mrow[4];
+            bool rok[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t i = row0 + rg + 32 * k;
+                rok[k] = i < p.n;
+                mrow[k] = p.M + (rok[k] ? i : 0) * p.n + kq * 8;
+            }
+            // this thread's 4 x 8 values of tile t (zero past row or column n), streaming loads
+            auto fetch = [&](int t, float4 (&b)[8]) {
+                const int64_t j = (int64_t)t * TJ + kq * 8;
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float *src = mrow[k] + (int64_t)t * TJ;
+                    if (p.vec4) {
+                        // n % 4 == 0 and j % 8 == 0: each float4 lies wholly inside or past column n
+                        b[2 * k] = (rok[k] && j < p.n) ? __ldcs(reinterpret_cast<const float4 *>(src)) : z;
+                        b[2 * k + 1] =
+                            (rok[k] && j + 4 < p.n) ? __ldcs(reinterpret_cast<const float4 *>(src + 4)) : z;
+                    } else {
+                        float e[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) e[q] = (rok[k] && j + q < p.n) ? __ldcs(src + q) : 0.f;
+                        b[2 * k] = make_float4(e[0], e[1], e[2], e[3]);
+                        b[2 * k + 1] = make_float4(e[4], e[5], e[6], e[7]);
+                    }
+                }
+            };
+            constexpr int PD = 3;  // tiles in flight per thread
+            float4 buf[PD][8];
+#pragma unroll
+            for (int u = 0; u < PD; ++u)
+                if (u < T) fetch(u, buf[u]);
+            for (int t0 = 0; t0 < T && ok; t0 += PD) {
+#pragma unroll
+                for (int ph = 0; ph < PD; ++ph) {
+                    const int t = t0 + ph;
+                    if (t >= T) break;
+                    const int sa = t % SA;
+                    if (DRAIN && t % KCH == KCH / 2 && t >= KCH + KCH / 2) {
+                        if (!drain(drained)) {
+                            ok = false;
+                            break;
+                        }
+                        ++drained;
+                    }
+                    if (t >= SA && !mbar_wait(&aempty[sa], ((t / SA) - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *ast = abase + (size_t)sa * L.a_bytes;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float4 v0 = buf[ph][2 * k], v1 = buf[ph][2 * k + 1];
+                        const float2 f[4] = {make_float2(v0.x * ms, v0.y * ms), make_float2(v0.z * ms, v0.w * ms),
+                                             make_float2(v1.x * ms, v1.y * ms), make_float2(v1.z * ms, v1.w * ms)};
+                        uint32_t w[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) w[q] = pack2<BF16>(f[q].x, f[q].y);
+                        const int r = rg + 32 * k;
+                        const size_t off = (size_t)(r >> 3) * 1024 + (size_t)kq * 128 + (size_t)(r & 7) * 16;
+                        *reinterpret_cast<uint4 *>(ast + off) = make_uint4(w[0], w[1], w[2], w[3]);
+                        if (NPROD == 3) {
+                            const float2 m1 = make_float2(-1.f, -1.f);
+                            uint32_t l[4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const float2 rq = __ffma2_rn(unpack2<BF16>(w[q]), m1, f[q]);  // m - hi
+                                l[q] = pack2<BF16>(rq.x, rq.y);
+                            }
+                            *reinterpret_cast<uint4 *>(ast + A_BYTES + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                        }
+                    }
+                    fence_async_smem();
+                    mbar_arrive(&afull[sa]);
+                    if (t + PD < T) fetch(t + PD, buf[ph]);
+                }
+            }
+        }
+        for (int t = 0; t < T && !FROMM; ++t) {
             const int sl = t % SL, sa = t % SA;
             if (DRAIN && t % KCH == KCH / 2 && t >= KCH + KCH / 2) {
                 // chunk t / KCH - 1 finished half a chunk ago
@@ -323,6 +417,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
             atomicOr(s_err, ERR_TIMEOUT);
         } else {
             const int64_t i = row0 + quad * 32 + lane;
+            const float post = FROMM ? __ldg(p.mscale + 1) : 1.f;  // undo the scale of M
             for (int c8 = halfc * ncol_half; c8 < (halfc + 1) * ncol_half; c8 += 8) {
                 float v[8];
                 if (DRAIN) {
@@ -336,8 +431,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) kz_tc_kernel(TcParams p, Layout L
                     for (int q = 0; q < 8; ++q) {
                         const int col = p.c0 + c8 + q;
                         if (c8 + q < p.N && col < p.c) {
-                            const float vin = p.V[i * p.c + col];
-                            p.W[i * p.c + col] = v[q] * p.variance * p.colinv[c8 + q] + p.noise * vin;
+                            if (FROMM) {
+                                p.W[i * p.c + col] = v[q] * post * p.colinv[c8 + q];
+                            } else {
+                                const float vin = p.V[i * p.c + col];
+                                p.W[i * p.c + col] = v[q] * p.variance * p.colinv[c8 + q] + p.noise * vin;
+                            }
                         }
                     }
                 }
@@ -399,6 +498,28 @@ __global__ void colscale_kernel(const float *part, int nb, int N, float *scale, 
     colinv[col] = 1.0f / s;
 }
 
+// Scale of a stored M: the power of two s with max_i |M_ii| s < 1 (s = 1 when the
+// diagonal is zero or not finite); for a positive semidefinite M every entry
+// satisfies |M_ij| <= max_i M_ii, so every scaled entry lies in [-1, 1].
+__global__ void diag_scale_kernel(const float *M, int64_t n, float *mscale) {
+    __shared__ float red[256];
+    float m = 0.f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(M[i * n + i]));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float mx = red[0];
+        int e = 0;
+        if (mx > 0.f && isfinite(mx)) frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+        mscale[0] = ldexpf(1.0f, -e);
+        mscale[1] = ldexpf(1.0f, e);
+    }
+}
+
 // Operand image of V: per j-tile t, per product half (hi, lo), N rows (columns of V)
 // x 64 K values in the canonical K-major no-swizzle layout:
 // byte offset (col/8)*1024 + (jj/8)*128 + (col%8)*16 + (jj%8)*2.
@@ -458,19 +579,19 @@ int stages_for(int N, int d, int nprod) {
     return 2;
 }
 
-template <int KIND, int DC, int NPROD, bool BF16, bool DRAIN>
+template <int KIND, int DC, int NPROD, bool BF16, bool DRAIN, bool FROMM = false>
 int launch_main(const TcParams &p, const Layout &L, int nblocks, cudaStream_t st) {
-    auto fn = kz_tc_kernel<KIND, DC, NPROD, BF16, DRAIN>;
+    auto fn = kz_tc_kernel<KIND, DC, NPROD, BF16, DRAIN, FROMM>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) {
         set_error("kz_tc: cannot reserve %d bytes of shared memory: %s", L.total, cudaGetErrorString(e));
         return LD_ERR_CUDA;
     }
     const double nn = (double)p.n * (double)p.n;
-    const int slot = prof_begin_launch(st, PROF_KZ_TC, nn, 2.0 * nn * p.N * NPROD);
+    const int slot = prof_begin_launch(st, FROMM ? PROF_DENSE : PROF_KZ_TC, nn, 2.0 * nn * p.N * NPROD);
     fn<<<nblocks, NTHREADS, L.total, st>>>(p, L);
     prof_end_launch(st, slot);
-    return check_launch("kz_tc_kernel");
+    return check_launch(FROMM ? "kz_tc_kernel (stored M)" : "kz_tc_kernel");
 }
 
 template <int KIND, int NPROD, bool BF16>
@@ -492,6 +613,25 @@ int launch_d(const TcParams &p, const Layout &L, int nblocks, cudaStream_t st) {
         case 4: return launch_main<KIND, 4, NPROD, BF16, false>(p, L, nblocks, st);
         default: return launch_main<KIND, 0, NPROD, BF16, false>(p, L, nblocks, st);
     }
+}
+
+// Column scales and the operand image of columns c0 .. c0 + N - 1 of V.
+int prep_chunk(const float *V, int64_t n, int c, int c0, int N, int64_t ntiles, int nprod, bool bf16, float *part,
+               float *scale, float *colinv, uint8_t *img, cudaStream_t st) {
+    const int nb = 256;
+    colmax_kernel<<<nb, MAX_N, 0, st>>>(V, n, c, c0, N, part);
+    colscale_kernel<<<1, MAX_N, 0, st>>>(part, nb, N, scale, colinv);
+    const int64_t nthr = (int64_t)ntiles * N * 8;
+    const unsigned gb = (unsigned)((nthr + 255) / 256);
+    if (bf16) image_kernel<true, 1><<<gb, 256, 0, st>>>(V, n, c, c0, N, (int)ntiles, scale, img);
+    else if (nprod == 3) image_kernel<false, 3><<<gb, 256, 0, st>>>(V, n, c, c0, N, (int)ntiles, scale, img);
+    else image_kernel<false, 1><<<gb, 256, 0, st>>>(V, n, c, c0, N, (int)ntiles, scale, img);
+    return check_launch("kz_tc prep", 3);
+}
+
+// TMEM columns: the next power of two >= cols (at least 32)
+int tmem_cols(int cols) {
+    return cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512)));
 }
 
 }  // namespace
@@ -553,15 +693,7 @@ int kz_tc(const float *Xs, int64_t n, int d, int kind, double variance, double n
         LD_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
         for (int c0 = 0; c0 < c; c0 += MAX_N) {
             const int N = chunk_N(std::min(MAX_N, c - c0));
-            const int nb = 256;
-            colmax_kernel<<<nb, MAX_N, 0, st>>>(V, n, c, c0, N, part);
-            colscale_kernel<<<1, MAX_N, 0, st>>>(part, nb, N, scale, colinv);
-            const int64_t nthr = (int64_t)ntiles * N * 8;
-            const unsigned gb = (unsigned)((nthr + 255) / 256);
-            if (bf16) image_kernel<true, 1><<<gb, 256, 0, st>>>(V, n, c, c0, N, (int)ntiles, scale, img);
-            else if (nprod == 3) image_kernel<false, 3><<<gb, 256, 0, st>>>(V, n, c, c0, N, (int)ntiles, scale, img);
-            else image_kernel<false, 1><<<gb, 256, 0, st>>>(V, n, c, c0, N, (int)ntiles, scale, img);
-            LD_TRY(check_launch("kz_tc prep", 3));
+            LD_TRY(prep_chunk(V, n, c, c0, N, ntiles, nprod, bf16, part, scale, colinv, img, st));
             TcParams p;
             p.Xp = Xp;
             p.img = img;
@@ -574,11 +706,14 @@ int kz_tc(const float *Xs, int64_t n, int d, int kind, double variance, double n
             p.c0 = c0;
             p.N = N;
             const int tcols = (nprod == 3 && N <= DRAIN_MAX_N) ? 2 * N : N;  // ping-pong buffers
-            p.ncols_tmem = tcols <= 32 ? 32 : (tcols <= 64 ? 64 : (tcols <= 128 ? 128 : (tcols <= 256 ? 256 : 512)));
+            p.ncols_tmem = tmem_cols(tcols);
             p.ntiles = (int)ntiles;
             p.variance = (float)variance;
             p.noise = (float)noise;
             p.err = err;
+            p.M = nullptr;
+            p.mscale = nullptr;
+            p.vec4 = 0;
             Layout L = make_layout(N, d, nprod, stages_for(N, d, nprod));
             // keep (CTAs per SM) x (TMEM columns) <= 512: reserve enough shared memory
             const int max_ctas = std::max(1, 512 / p.ncols_tmem);
@@ -600,6 +735,97 @@ int kz_tc(const float *Xs, int64_t n, int d, int kind, double variance, double n
         LD_CHECK_CUDA(cudaStreamSynchronize(st));
         if (herr) {
             set_error("kz_tc: a device-side wait timed out (error word %d)", herr);
+            return LD_ERR_DEVICE_TIMEOUT;
+        }
+        return LD_OK;
+    }();
+    ws.off = mark;
+    return code;
+}
+
+// ------------------------------------------------------- stored dense M
+size_t dense_tc_workspace(int64_t n, int c, int precision) {
+    const int64_t ntiles = (n + TJ - 1) / TJ;
+    const int N = chunk_N(c);
+    const int nprod = nprod_of(precision);
+    Arena a;
+    a.measuring = true;
+    a.take<uint8_t>((size_t)ntiles * (nprod == 3 ? 2 : 1) * N * TJ * 2);  // operand image
+    a.take<float>(MAX_N);                                                // scale
+    a.take<float>(MAX_N);                                                // 1/scale
+    a.take<float>((size_t)256 * MAX_N);                                  // colmax partials
+    a.take<float>(4);                                                    // scale of M
+    a.take<int>(4);                                                      // error word
+    return a.off;
+}
+
+int dense_tc(const float *M, int64_t n, const float *V, float *W, int c, int precision, Arena &ws,
+             cudaStream_t st) {
+    if (n == 0 || c == 0) return LD_OK;
+    if (precision != LD_F16_TC && precision != LD_BF16_TC && precision != LD_F16X3_TC) {
+        set_error("dense_tc: not a tensor-core precision");
+        return LD_ERR_INVALID;
+    }
+    const int64_t ntiles = (n + TJ - 1) / TJ;
+    const int nprod = nprod_of(precision);
+    const bool bf16 = precision == LD_BF16_TC;
+    const int Nmax = chunk_N(c);
+    const size_t mark = ws.off;
+    uint8_t *img = ws.take<uint8_t>((size_t)ntiles * (nprod == 3 ? 2 : 1) * Nmax * TJ * 2);
+    float *scale = ws.take<float>(MAX_N);
+    float *colinv = ws.take<float>(MAX_N);
+    float *part = ws.take<float>((size_t)256 * MAX_N);
+    float *mscale = ws.take<float>(4);
+    int *err = ws.take<int>(4);
+    if (ws.overflow || !img) {
+        set_error("dense_tc: workspace too small");
+        ws.off = mark;
+        return LD_ERR_WORKSPACE;
+    }
+    int code = [&]() -> int {
+        diag_scale_kernel<<<1, 256, 0, st>>>(M, n, mscale);
+        LD_TRY(check_launch("diag_scale"));
+        LD_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+        const bool vec4 = n % 4 == 0 && reinterpret_cast<uintptr_t>(M) % 16 == 0;
+        for (int c0 = 0; c0 < c; c0 += MAX_N) {
+            const int N = chunk_N(std::min(MAX_N, c - c0));
+            LD_TRY(prep_chunk(V, n, c, c0, N, ntiles, nprod, bf16, part, scale, colinv, img, st));
+            TcParams p;
+            p.Xp = nullptr;
+            p.img = img;
+            p.V = V;
+            p.colinv = colinv;
+            p.W = W;
+            p.n = n;
+            p.d = 1;
+            p.c = c;
+            p.c0 = c0;
+            p.N = N;
+            const bool drain = nprod == 3 && N <= DRAIN_MAX_N;
+            p.ncols_tmem = tmem_cols(drain ? 2 * N : N);
+            p.ntiles = (int)ntiles;
+            p.variance = 1.f;
+            p.noise = 0.f;
+            p.err = err;
+            p.M = M;
+            p.mscale = mscale;
+            p.vec4 = vec4 ? 1 : 0;
+            // no point tiles in the load stages; one CTA per SM (its registers hold three
+            // tiles of M per thread in flight)
+            Layout L = make_layout(N, 0, nprod, stages_for(N, 0, nprod));
+            const int max_ctas = std::max(1, 512 / p.ncols_tmem);  // TMEM columns per SM
+            L.total = std::max(L.total, (228 * 1024) / (max_ctas + 1) + 1024);
+            const int nblocks = (int)((n + TM - 1) / TM);
+            if (bf16) LD_TRY((launch_main<LD_RBF, 1, 1, true, false, true>(p, L, nblocks, st)));
+            else if (nprod == 1) LD_TRY((launch_main<LD_RBF, 1, 1, false, false, true>(p, L, nblocks, st)));
+            else if (drain) LD_TRY((launch_main<LD_RBF, 1, 3, false, true, true>(p, L, nblocks, st)));
+            else LD_TRY((launch_main<LD_RBF, 1, 3, false, false, true>(p, L, nblocks, st)));
+        }
+        int herr = 0;
+        LD_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LD_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (herr) {
+            set_error("dense_tc: a device-side wait timed out (error word %d)", herr);
             return LD_ERR_DEVICE_TIMEOUT;
         }
         return LD_OK;

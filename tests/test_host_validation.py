@@ -88,3 +88,12 @@ def test_profile_kernel_id_check(lib):
                                  ctypes.byref(flops)) == _lib.LD_ERR_INVALID
     assert lib.ld_profile_kernel(1, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(pairs),
                                  ctypes.byref(flops)) == _lib.LD_OK
+
+
+def test_dense_product_argument_checks(lib):
+    W = ctypes.c_void_p(0x2000)
+    f16x3 = api.PRECISIONS["f16x3_tc"]
+    for n, c, prec in ((0, 4, f16x3), (10, 0, f16x3), (10, 4, 9), (10, 4, -1), (10, 4097, f16x3)):
+        assert lib.ld_dense_kz(FAKE, n, FAKE, W, c, prec, None) == _lib.LD_ERR_INVALID, (n, c, prec)
+    assert b"ld_dense_kz" in lib.ld_last_error()
+    assert lib.ld_dense_kz(FAKE, 10, FAKE, FAKE, 4, f16x3, None) == _lib.LD_ERR_INVALID  # W aliasing V
