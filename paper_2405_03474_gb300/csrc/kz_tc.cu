@@ -24,8 +24,8 @@
 // variance and the variance is applied in the epilogue.
 //
 // The same pipeline serves a stored dense M = K + noise I (FROMM): the eval warps
-// then read their 4 rows x 8 columns of each 128 x 64 tile of M from HBM (streaming
-// loads, three tiles in flight per thread), scale them by a power of two that
+// then read 4 x 8 values each of every 128 x 64 tile of M from HBM (streaming
+// loads, three tiles in flight per thread, 8 rows x 128 bytes per warp load), scale them by a power of two that
 // brings max |M_ii| below 1 and round/split them exactly as computed values; the
 // producer streams only the operand image of V.  One pass reads M once, so the
 // product is bound by HBM instead of the FP32 pipes of the SIMT GEMM.
@@ -258,22 +258,27 @@ __global__ void __launch_bounds__(NTHREADS, FROMM ? 1 : 2) kz_tc_kernel(TcParams
         int drained = 0;                     // chunks already drained
         bool ok = true;
         if (FROMM) {
-            // stored M: rows rg + 32 k of the block, columns 8 kq .. 8 kq + 7 of each tile
+            // stored M: unit k of this thread is row mr(k) = 16 warp + 8 (k >> 1) + lane % 8 and
+            // the 8 columns 8 mq(k) .. 8 mq(k) + 7 of each tile, mq(k) = 4 (k & 1) + lane / 8, so
+            // one warp-wide load covers 8 rows x 128 contiguous bytes (8 cache lines) and the
+            // 8 lanes of each 16-byte store phase write 8 distinct rows (no bank conflicts)
             const float ms = __ldg(p.mscale);
+            auto mr = [&](int k) { return 16 * warp + 8 * (k >> 1) + (lane & 7); };
+            auto mq = [&](int k) { return 4 * (k & 1) + (lane >> 3); };
             const float *mrow[4];
             bool rok[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int64_t i = row0 + rg + 32 * k;
+                const int64_t i = row0 + mr(k);
                 rok[k] = i < p.n;
-                mrow[k] = p.M + (rok[k] ? i : 0) * p.n + kq * 8;
+                mrow[k] = p.M + (rok[k] ? i : 0) * p.n + mq(k) * 8;
             }
             // this thread's 4 x 8 values of tile t (zero past row or column n), streaming loads
             auto fetch = [&](int t, float4 (&b)[8]) {
-                const int64_t j = (int64_t)t * TJ + kq * 8;
                 const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
+                    const int64_t j = (int64_t)t * TJ + mq(k) * 8;
                     const float *src = mrow[k] + (int64_t)t * TJ;
                     if (p.vec4) {
                         // n % 4 == 0 and j % 8 == 0: each float4 lies wholly inside or past column n
@@ -320,8 +325,8 @@ __global__ void __launch_bounds__(NTHREADS, FROMM ? 1 : 2) kz_tc_kernel(TcParams
                         uint32_t w[4];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) w[q] = pack2<BF16>(f[q].x, f[q].y);
-                        const int r = rg + 32 * k;
-                        const size_t off = (size_t)(r >> 3) * 1024 + (size_t)kq * 128 + (size_t)(r & 7) * 16;
+                        const int r = mr(k);
+                        const size_t off = (size_t)(r >> 3) * 1024 + (size_t)mq(k) * 128 + (size_t)(r & 7) * 16;
                         *reinterpret_cast<uint4 *>(ast + off) = make_uint4(w[0], w[1], w[2], w[3]);
                         if (NPROD == 3) {
                             const float2 m1 = make_float2(-1.f, -1.f);
