@@ -27,7 +27,11 @@ void count_launches(int k) { g_launches += k; }
 int prof_begin_launch(cudaStream_t st, int kernel, double pairs, double mma_flops) {
     if (!g_on) return -1;
     Rec r;
-    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
+    if (cudaEventCreate(&r.a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&r.b) != cudaSuccess) {
+        cudaEventDestroy(r.a);
+        return -1;
+    }
     r.pairs = pairs;
     r.flops = mma_flops;
     r.kernel = kernel >= 0 && kernel < PROF_KERNELS ? kernel : 0;
