@@ -119,8 +119,14 @@ def ld_dense_materialize(X, kernel, precision="fp32", stream=None):
 
 
 def ld_dense_kz(M, V, precision="fp32", stream=None):
-    """W = M V for a stored dense M."""
+    """W = M V for a stored dense M (n-by-n; float64 for fp64, else float32; positive
+    semidefinite for the tensor-core precisions, as every K + noise I is)."""
     lib = _lib.load()
+    want = torch.float64 if _prec(precision) == _lib.FP64 else torch.float32
+    if M.dtype != want or M.dim() != 2 or M.shape[0] != M.shape[1]:
+        raise ValueError("M must be an n-by-n %s tensor" % want)
+    if V.dtype != want or V.dim() != 2 or V.shape[0] != M.shape[0]:
+        raise ValueError("V must be an n-by-c %s tensor" % want)
     _need_cuda(M, V)
     W = torch.empty_like(V)
     check(lib.ld_dense_kz(_ptr(M), M.shape[0], _ptr(V), _ptr(W), V.shape[1], _prec(precision), _stream(stream)),

@@ -97,3 +97,18 @@ def test_dense_product_argument_checks(lib):
         assert lib.ld_dense_kz(FAKE, n, FAKE, W, c, prec, None) == _lib.LD_ERR_INVALID, (n, c, prec)
     assert b"ld_dense_kz" in lib.ld_last_error()
     assert lib.ld_dense_kz(FAKE, 10, FAKE, FAKE, 4, f16x3, None) == _lib.LD_ERR_INVALID  # W aliasing V
+
+
+def test_dense_binding_checks_dtypes_and_shapes():
+    torch = pytest.importorskip("torch")
+    M32, V32 = torch.zeros(6, 6), torch.zeros(6, 2)
+    with pytest.raises(ValueError, match="M must be"):
+        api.ld_dense_kz(M32.double(), V32, "f16x3_tc")
+    with pytest.raises(ValueError, match="M must be"):
+        api.ld_dense_kz(torch.zeros(6, 5), V32, "fp32")
+    with pytest.raises(ValueError, match="V must be"):
+        api.ld_dense_kz(M32, torch.zeros(5, 2), "fp32")
+    with pytest.raises(ValueError, match="V must be"):
+        api.ld_dense_kz(M32.double(), V32, "fp64")
+    with pytest.raises(ValueError, match="CUDA"):  # well-formed, but host tensors
+        api.ld_dense_kz(M32, V32, "bf16_tc")
