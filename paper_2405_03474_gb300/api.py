@@ -98,7 +98,10 @@ def ld_kz_dl(X, V, kernel, precision="fp32", stream=None):
     lib = _lib.load()
     X = _points(X)
     p = _prec(precision)
+    want = torch.float64 if p == _lib.FP64 else torch.float32
     _need_cuda(V)
+    if V.dtype != want or V.dim() != 2 or V.shape[0] != X.shape[0]:
+        raise ValueError("V must be n-by-c %s" % want)
     W = torch.empty_like(V)
     Wdl = torch.empty_like(V)
     n, d = X.shape
@@ -213,7 +216,11 @@ class Precond:
         return A, D, ld.value
 
     def apply(self, V, transpose=False, stream=None):
+        """L^-1 V (or L^-T V): V is n-by-c, float64 for an fp64 handle, else float32."""
         lib = _lib.load()
+        want = torch.float64 if self.precision == _lib.FP64 else torch.float32
+        if V.dtype != want or V.dim() != 2 or V.shape[0] != self.n:
+            raise ValueError("V must be an n-by-c %s tensor" % want)
         _need_cuda(V)
         W = torch.empty_like(V)
         check(lib.precond_apply(self._h, int(transpose), _ptr(V), _ptr(W), V.shape[1], _stream(stream)),
