@@ -61,15 +61,18 @@ class Estimator:
 
 def generate_labels(est, thetas, checkpoint=None, every=32, log=None):
     """Labels est(theta) for each row of thetas, saved every `every` labels to
-    `checkpoint` (.npz with thetas, labels, done) and resumed from it."""
+    `checkpoint` (.npz with thetas, labels, done) and resumed from it: the labels
+    already done are reused when their thetas are the first rows of `thetas`, so a
+    job also extends a shorter run of the same Sobol sequence."""
     thetas = np.asarray(thetas, dtype=np.float64)
     labels = np.full(len(thetas), np.nan)
     done = 0
     if checkpoint and os.path.exists(checkpoint):
         z = np.load(checkpoint)
-        if z["thetas"].shape == thetas.shape and np.array_equal(z["thetas"], thetas):
-            labels[:] = z["labels"]
-            done = int(z["done"])
+        k = min(int(z["done"]), len(thetas))
+        if z["thetas"].shape[1:] == thetas.shape[1:] and np.array_equal(z["thetas"][:k], thetas[:k]):
+            labels[:k] = z["labels"][:k]
+            done = k
     t0 = time.perf_counter()
     for i in range(done, len(thetas)):
         labels[i] = est(thetas[i])
