@@ -300,7 +300,7 @@ int ld_profile_begin(void);
 int ld_profile_end(double *kz_ms, int64_t *kz_launches, double *kz_pairs, double *kz_mma_flops);
 /* The same totals of the last closed window for one kernel: 0 the general
  * tensor-core product, 1 the symmetric tensor-core product, 2 the SIMT product,
- * 3 the stored dense product, 4 the one-pass wide (256 < c <= 512) tensor-core
+ * 3 the stored dense product (CUDA-core GEMM or tensor cores), 4 the one-pass wide (256 < c <= 512) tensor-core
  * product.  LD_ERR_INVALID for another id. */
 int ld_profile_kernel(int32_t kernel, double *ms, int64_t *launches, double *pairs, double *mma_flops);
 
