@@ -26,7 +26,8 @@ precond    Randomized truncated SVD preconditioner P = D + A A^T (Section 2,
            Halko et al. Algorithms 4.1/4.4/5.3; Appendix list), its symmetric
            factor L and log det P.
 estimator  Algorithm 1 (literal: Lanczos + Thomas) and its converged form
-           (exact shifted solves), plus exact Cholesky log det.
+           (exact shifted solves), the multi-shift CG recurrence the device
+           runs (Section 2, after Jegerlehner), plus exact Cholesky log det.
 gradient   Gradient of the estimator with P frozen, and the exact gradient
            tr(M^-1 dM/dtheta).
 mlp        FP64 forward/backward of the 4-128-128-128-1 GELU surrogate MLP.

@@ -142,6 +142,50 @@ def estimate_slq(B, logdet_P, Z, t):
     return float(logdet_P + np.mean(per)), per
 
 
+def multishift_cg(B, z, deltas, iters):
+    """Shifted solves x_j ~ (B + delta_j I)^-1 z from one CG run on the seed system B x = z
+    (Section 2's multi-shift paragraph, after Jegerlehner): the shifted residuals stay
+    collinear with the seed residual, r^j_k = zeta^j_k r_k, and
+
+        zeta^j_{k+1} = zeta^j_k zeta^j_{k-1} a_{k-1}
+                       / (a_k b_{k-1} (zeta^j_{k-1} - zeta^j_k) + zeta^j_{k-1} a_{k-1} (1 + delta_j a_k)),
+        a^j_k = a_k zeta^j_{k+1} / zeta^j_k,   b^j_k = b_k (zeta^j_{k+1} / zeta^j_k)^2,
+        x^j += a^j_k p^j_k,   p^j_{k+1} = zeta^j_{k+1} r_{k+1} + b^j_k p^j_k,
+
+    with a_k, b_k the seed system's CG coefficients, zeta^j_{-1} = zeta^j_0 = 1, a_{-1} = 1,
+    b_{-1} = 0.  Returns the len(deltas)-by-n shifted iterates after `iters` steps, or fewer
+    once the seed residual is below 1e-16 |z| (the iterates are converged there, and further
+    steps would drive the zeta to underflow)."""
+    B = np.asarray(B, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    deltas = np.asarray(deltas, dtype=np.float64)
+    m = len(deltas)
+    r = z.copy()
+    p = z.copy()
+    rho = float(r @ r)
+    xs = np.zeros((m, len(z)))
+    ps = np.tile(z, (m, 1))
+    zeta, zeta_prev = np.ones(m), np.ones(m)
+    a_prev, b_prev = 1.0, 0.0
+    rho0 = rho
+    for _ in range(iters):
+        if rho <= 1e-32 * rho0:
+            break
+        Bp = B @ p
+        a = rho / float(p @ Bp)
+        zeta_next = zeta * zeta_prev * a_prev / (a * b_prev * (zeta_prev - zeta)
+                                                 + zeta_prev * a_prev * (1.0 + deltas * a))
+        xs += (a * zeta_next / zeta)[:, None] * ps
+        r = r - a * Bp
+        rho_next = float(r @ r)
+        b = rho_next / rho
+        ps = zeta_next[:, None] * r[None, :] + (b * (zeta_next / zeta) ** 2)[:, None] * ps
+        p = r + b * p
+        zeta_prev, zeta = zeta, zeta_next
+        a_prev, b_prev, rho = a, b, rho_next
+    return xs
+
+
 def rk_bias(B, k):
     """Exact r_k bias of the trace term: sum_i [log lam_i(B) - r_k(lam_i(B))]."""
     lam = np.linalg.eigvalsh(B)

@@ -140,3 +140,26 @@ def test_slq_with_full_lanczos_is_exact_quadratic_form():
     Zall = np.array(list(itertools.product([-1.0, 1.0], repeat=n2))).T
     est, _ = estimator.estimate_slq(precond.operator_B(M2, F2), 0.0, Zall, n2)
     assert est == pytest.approx(estimator.logdet_exact(M2), rel=1e-10)
+
+
+def test_multishift_cg_equals_direct_shifted_solves():
+    # One CG run on the seed system gives every shifted solution (Section 2, after
+    # Jegerlehner); at the r_3 / r_5 pole spacings and after enough steps the iterates
+    # equal (B + delta I)^-1 z from a dense solve.
+    n = 80
+    X = inputs.points(n, 2, "uniform", seed=14)
+    M = kernels.kernel_matrix(X, kernels.MATERN52, 0.3, 1.0, 5e-2)
+    F = precond.factors(*precond.build(M, rademacher_block(2, n, 12), 2, 5e-2))
+    B = precond.operator_B(M, F)
+    z = rademacher_block(6, n, 1)[:, 0]
+    for k in (3, 5):
+        _, _, sigma = coeffs.rk_coeffs(k)
+        seed = B + sigma[0] * np.eye(n)
+        deltas = sigma - sigma[0]
+        xs = estimator.multishift_cg(seed, z, deltas, 3 * n)
+        for j, dj in enumerate(deltas):
+            ref = np.linalg.solve(seed + dj * np.eye(n), z)
+            np.testing.assert_allclose(xs[j], ref, rtol=1e-9, atol=1e-11 * np.abs(ref).max())
+        # and the quadratic forms are those of the converged estimator
+        q = z @ xs.T
+        np.testing.assert_allclose(q, estimator.shifted_quadforms(B, z[:, None], sigma)[0], rtol=1e-9)
