@@ -142,6 +142,34 @@ def estimate_slq(B, logdet_P, Z, t):
     return float(logdet_P + np.mean(per)), per
 
 
+def cg_tridiagonal(B, z, t):
+    """The Lanczos tridiagonal of (B, z) rebuilt from t steps of plain CG on B x = z
+    (the equivalence behind Section 2's multi-shift reading of Algorithm 1): with the CG
+    step sizes a_k and ratios b_k = rho_{k+1} / rho_k,
+
+        T_kk = 1 / a_k + b_{k-1} / a_{k-1}   (no second term for k = 0),
+        T_k,k+1 = sqrt(b_k) / a_k.
+
+    Returns (diag, offdiag) like ``lanczos``."""
+    B = np.asarray(B, dtype=np.float64)
+    r = np.asarray(z, dtype=np.float64).copy()
+    p = r.copy()
+    rho = float(r @ r)
+    a = np.zeros(t)
+    b = np.zeros(t)
+    for k in range(t):
+        Bp = B @ p
+        a[k] = rho / float(p @ Bp)
+        r = r - a[k] * Bp
+        rho_next = float(r @ r)
+        b[k] = rho_next / rho
+        p = r + b[k] * p
+        rho = rho_next
+    diag = 1.0 / a
+    diag[1:] += b[:-1] / a[:-1]
+    return diag, np.sqrt(b[:-1]) / a[:-1]
+
+
 def multishift_cg(B, z, deltas, iters):
     """Shifted solves x_j ~ (B + delta_j I)^-1 z from one CG run on the seed system B x = z
     (Section 2's multi-shift paragraph, after Jegerlehner): the shifted residuals stay

@@ -163,3 +163,18 @@ def test_multishift_cg_equals_direct_shifted_solves():
         # and the quadratic forms are those of the converged estimator
         q = z @ xs.T
         np.testing.assert_allclose(q, estimator.shifted_quadforms(B, z[:, None], sigma)[0], rtol=1e-9)
+
+
+def test_tridiagonal_from_cg_coefficients_equals_lanczos():
+    # CG and Lanczos build the same Krylov space: T from the CG scalars equals the
+    # Lanczos T of the same start vector (before the basis loses orthogonality).
+    n, t = 120, 15
+    X = inputs.points(n, 3, "uniform", seed=15)
+    M = kernels.kernel_matrix(X, kernels.RBF, 0.35, 1.0, 2e-2)
+    F = precond.factors(*precond.build(M, rademacher_block(2, n, 10), 2, 2e-2))
+    B = precond.operator_B(M, F) + 0.5 * np.eye(n)
+    z = rademacher_block(8, n, 1)[:, 0]
+    a, bt, _ = estimator.lanczos(B, z, t)
+    d, off = estimator.cg_tridiagonal(B, z, t)
+    np.testing.assert_allclose(d, a, rtol=1e-10)
+    np.testing.assert_allclose(off, bt, rtol=1e-9)

@@ -59,6 +59,10 @@ MUTANTS = [
       "test_oracle_estimator::test_slq_with_full_lanczos_is_exact_quadratic_form", id="slq-transposed-eigvec"),
     P("oracle.estimator", "return 2.0 * float(np.sum(np.log(np.diag(L))))", "return float(np.sum(np.log(np.diag(L))))",
       "test_oracle_estimator::test_logdet_exact_against_lu_and_diagonal", id="cholesky-logdet-factor"),
+    P("oracle.estimator", "diag[1:] += b[:-1] / a[:-1]", "diag[1:] += b[1:] / a[1:]",
+      "test_oracle_estimator::test_tridiagonal_from_cg_coefficients_equals_lanczos", id="cg-tridiagonal-index"),
+    P("oracle.estimator", "np.sqrt(b[:-1]) / a[:-1]", "b[:-1] / a[:-1]",
+      "test_oracle_estimator::test_tridiagonal_from_cg_coefficients_equals_lanczos", id="cg-offdiagonal-sqrt"),
     P("oracle.estimator", "zeta_prev * a_prev * (1.0 + deltas * a))", "zeta_prev * a_prev * (1.0 - deltas * a))",
       "test_oracle_estimator::test_multishift_cg_equals_direct_shifted_solves", id="multishift-zeta-sign"),
     P("oracle.estimator", "(b * (zeta_next / zeta) ** 2)", "(b * (zeta_next / zeta))",
