@@ -178,3 +178,22 @@ def test_tridiagonal_from_cg_coefficients_equals_lanczos():
     d, off = estimator.cg_tridiagonal(B, z, t)
     np.testing.assert_allclose(d, a, rtol=1e-10)
     np.testing.assert_allclose(off, bt, rtol=1e-9)
+
+
+@pytest.mark.parametrize("k", coeffs.ORDERS)
+def test_lanczos_exact_once_krylov_space_is_exhausted(k):
+    # B with m distinct eigenvalues: the Krylov space of any z has dimension <= m, so
+    # Algorithm 1 with t = m is Gauss quadrature with m nodes on an m-point measure,
+    # exact for the rational r_k: the literal estimate equals the converged one.
+    rng = np.random.default_rng(16)
+    n, lam = 60, np.array([0.3, 0.9, 1.7, 4.0, 11.0])
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    B = (U * np.repeat(lam, n // len(lam))) @ U.T
+    B = 0.5 * (B + B.T)
+    Z = rademacher_block(9, n, 4)
+    e_lit, p_lit, _ = estimator.estimate_lanczos(B, 0.0, Z, k, len(lam))
+    e_con, p_con, _ = estimator.estimate_converged(B, 0.0, Z, k)
+    np.testing.assert_allclose(p_lit, p_con, rtol=1e-10)
+    # with one step fewer the quadrature is not exact
+    _, p_short, _ = estimator.estimate_lanczos(B, 0.0, Z, k, len(lam) - 1)
+    assert np.max(np.abs(p_short - p_con)) > 1e-8 * np.max(np.abs(p_con))
