@@ -100,3 +100,17 @@ def test_plus_scaling_variant():
     np.testing.assert_array_equal(D2, np.full(n, a))
     F = precond.factors(A2, D2)
     assert F["logdet_P"] == pytest.approx(np.linalg.slogdet(a * np.eye(n) + A2 @ A2.T)[1], rel=1e-12)
+
+
+def test_rank_one_build_is_the_appendix_rank_one_preconditioner():
+    # The Appendix's rank-one preconditioner P = D + lambda v v^T with D = diag(M - lambda v v^T)
+    # is this build at rank 1: subspace iteration converges to the top eigenpair (lambda, v).
+    n = 250
+    X = inputs.points(n, 2, "uniform", seed=12)
+    M = kernels.kernel_matrix(X, kernels.MATERN52, 0.5, 1.0, 1e-2)
+    A, D = precond.build(M, rademacher_block(2, n, 1), 30, 1e-2)
+    lam, U = np.linalg.eigh(M)
+    v = U[:, -1]
+    np.testing.assert_allclose(A[:, 0] @ A[:, 0], lam[-1], rtol=1e-10)
+    np.testing.assert_allclose(np.abs(A[:, 0]) / np.sqrt(lam[-1]), np.abs(v), atol=1e-8)
+    np.testing.assert_allclose(D, np.maximum(np.diag(M - lam[-1] * np.outer(v, v)), 1e-2), rtol=1e-8)
