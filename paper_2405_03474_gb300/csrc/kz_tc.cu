@@ -25,10 +25,11 @@
 //
 // The same pipeline serves a stored dense M = K + noise I (FROMM): the eval warps
 // then read 4 x 8 values each of every 128 x 64 tile of M from HBM (streaming
-// loads, three tiles in flight per thread, 8 rows x 128 bytes per warp load), scale them by a power of two that
-// brings max |M_ii| below 1 and round/split them exactly as computed values; the
-// producer streams only the operand image of V.  One pass reads M once, so the
-// product is bound by HBM instead of the FP32 pipes of the SIMT GEMM.
+// loads, three tiles in flight per thread, 8 rows x 128 bytes per warp load),
+// scale them by a power of two that brings max |M_ii| below 1 and round/split
+// them exactly as computed values; the producer streams only the operand image
+// of V.  One pass reads M once, so the product is bound by HBM instead of the
+// FP32 pipes of the SIMT GEMM.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
