@@ -106,6 +106,20 @@ def thomas(lower, diag, upper, rhs):
     return x
 
 
+def step3_quadforms(a, bt, vn, sigma):
+    """Algorithm 1 step 3 for one probe v with |v| = vn and Lanczos tridiagonal
+    T = (diag a, offdiag bt): per shift, (T - alpha_j) w = |v| e_1 by Thomas
+    (alpha_j = -sigma_j), and the quadratic form v^T Q^T w = |v| e_1^T w."""
+    m = len(a)
+    e1 = np.zeros(m)
+    e1[0] = vn
+    out = np.empty(len(sigma))
+    for j, sj in enumerate(sigma):
+        w = thomas(bt, a + sj, bt, e1)
+        out[j] = vn * w[0]
+    return out
+
+
 def estimate_lanczos(B, logdet_P, Z, k, t):
     """Algorithm 1 taken literally: Lanczos (t steps) then Thomas per shift."""
     _, _, sigma = coeffs.rk_coeffs(k)
@@ -114,16 +128,62 @@ def estimate_lanczos(B, logdet_P, Z, k, t):
     q = np.empty((s, len(sigma)))
     for i in range(s):
         v = Z[:, i]
-        vn = np.linalg.norm(v)
         a, bt, _ = lanczos(B, v, t)
-        m = len(a)
-        e1 = np.zeros(m)
-        e1[0] = vn
-        for j, sj in enumerate(sigma):
-            w = thomas(bt, a + sj, bt, e1)  # (T - alpha_j) w = |v| e_1
-            q[i, j] = vn * w[0]             # v^T Q^T w = |v| e_1^T w
+        q[i] = step3_quadforms(a, bt, np.linalg.norm(v), sigma)
     est, per_probe = combine(logdet_P, Z, q, k)
     return est, per_probe, q
+
+
+def lanczos_block(apply, V, t):
+    """``lanczos`` for every column of V at once, for a B given only as a product:
+    ``apply(W)`` returns B W for an n-by-s block.  Column c runs its own recurrence
+    from V[:, c] / |V[:, c]| with full reorthogonalisation against its own basis, so
+    each of the t steps costs one block product instead of s single ones.  Returns
+    one (diag, offdiag) pair per column; a column stops early on an invariant
+    subspace like ``lanczos`` (its later columns of the block are zero)."""
+    V = np.asarray(V, dtype=np.float64)
+    n, s = V.shape
+    Q = np.zeros((s, t, n))
+    alpha = np.zeros((s, t))
+    beta = np.zeros((s, t))
+    m = np.full(s, t)
+    cur = V / np.linalg.norm(V, axis=0)[None, :]
+    live = np.ones(s, dtype=bool)
+    for k in range(t):
+        Q[:, k, :] = cur.T
+        W = apply(cur)
+        for c in range(s):
+            if not live[c]:
+                continue
+            w = W[:, c]
+            alpha[c, k] = cur[:, c] @ w
+            Qc = Q[c, :k + 1]
+            w = w - Qc.T @ (Qc @ w)
+            w = w - Qc.T @ (Qc @ w)
+            beta[c, k] = np.linalg.norm(w)
+            if k + 1 == t:
+                continue
+            if beta[c, k] <= 1e-14 * max(1.0, abs(alpha[c, k])):
+                m[c] = k + 1
+                live[c] = False
+                cur[:, c] = 0.0
+                continue
+            cur[:, c] = w / beta[c, k]
+    return [(alpha[c, :m[c]], beta[c, :m[c] - 1]) for c in range(s)]
+
+
+def estimate_lanczos_block(apply, logdet_P, Z, k, t):
+    """Algorithm 1 taken literally for a B given as a block product (``lanczos_block``
+    then ``step3_quadforms`` per probe).  Returns (estimate, per-probe brackets, q,
+    the per-probe tridiagonals)."""
+    _, _, sigma = coeffs.rk_coeffs(k)
+    Z = np.asarray(Z, dtype=np.float64)
+    tri = lanczos_block(apply, Z, t)
+    q = np.empty((Z.shape[1], len(sigma)))
+    for i, (a, bt) in enumerate(tri):
+        q[i] = step3_quadforms(a, bt, np.linalg.norm(Z[:, i]), sigma)
+    est, per_probe = combine(logdet_P, Z, q, k)
+    return est, per_probe, q, tri
 
 
 def estimate_slq(B, logdet_P, Z, t):
@@ -136,10 +196,16 @@ def estimate_slq(B, logdet_P, Z, t):
     for i in range(Z.shape[1]):
         v = Z[:, i]
         a, bt, _ = lanczos(B, v, t)
-        T = np.diag(a) + np.diag(bt, 1) + np.diag(bt, -1)
-        theta, V = np.linalg.eigh(T)
-        per[i] = float(v @ v) * float(np.sum(V[0] ** 2 * np.log(theta)))
+        per[i] = slq_form(a, bt, float(v @ v))
     return float(logdet_P + np.mean(per)), per
+
+
+def slq_form(a, bt, vn2):
+    """Gauss quadrature of v^T log(B) v from the Lanczos tridiagonal T of (B, v),
+    |v|^2 = vn2: T = V diag(theta) V^T, |v|^2 sum_k (e_1^T v_k)^2 log(theta_k)."""
+    T = np.diag(a) + np.diag(bt, 1) + np.diag(bt, -1)
+    theta, V = np.linalg.eigh(T)
+    return vn2 * float(np.sum(V[0] ** 2 * np.log(theta)))
 
 
 def cg_tridiagonal(B, z, t):

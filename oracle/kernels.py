@@ -18,6 +18,9 @@ Lengthscale derivatives (differentiating the forms above):
 
 and dk/dv = k / v, dM/dnu = I.
 """
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 RBF = 0
@@ -94,4 +97,24 @@ def kz_rows(X, V, rows, kind, lengthscale, variance, noise=0.0):
         Kb = kernel_of_r2(sqdist(X[rows], X[j0:j0 + chunk]), kind, lengthscale, variance)
         out += Kb @ V[j0:j0 + chunk]
     out += noise * V[rows]
+    return out
+
+
+def kz_matfree(X, V, kind, lengthscale, variance, noise=0.0, rows_per_task=128, threads=None):
+    """All rows of (K + noise I) V without forming K: ``kz_rows`` over consecutive
+    row ranges, the ranges spread over a thread pool (numpy releases the GIL in
+    its elementwise loops and BLAS calls, so the host cores share the work).
+    Each output row is computed exactly as ``kz_rows`` computes it."""
+    X = np.asarray(X, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    n = X.shape[0]
+    out = np.empty((n, V.shape[1]))
+    starts = list(range(0, n, rows_per_task))
+
+    def task(i0):
+        rows = np.arange(i0, min(n, i0 + rows_per_task))
+        out[rows] = kz_rows(X, V, rows, kind, lengthscale, variance, noise)
+
+    with ThreadPoolExecutor(threads or os.cpu_count() or 1) as ex:
+        list(ex.map(task, starts))
     return out

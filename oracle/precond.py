@@ -132,6 +132,12 @@ def operator_B(M, F):
     return 0.5 * (B + B.T)
 
 
+def operator_B_apply(matmul, F):
+    """B = L^-1 M L^-T as a block product, for an M given only as ``matmul(V)`` = M V
+    (the matrix-free form of ``operator_B``)."""
+    return lambda V: apply_Linv(F, matmul(apply_LinvT(F, V)))
+
+
 def identity(n):
     """P = I (Appendix "Identity"): A is n-by-0 and D = 1."""
     return np.zeros((n, 0)), np.ones(n)

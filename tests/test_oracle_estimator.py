@@ -197,3 +197,75 @@ def test_lanczos_exact_once_krylov_space_is_exhausted(k):
     # with one step fewer the quadrature is not exact
     _, p_short, _ = estimator.estimate_lanczos(B, 0.0, Z, k, len(lam) - 1)
     assert np.max(np.abs(p_short - p_con)) > 1e-8 * np.max(np.abs(p_con))
+
+
+def test_block_lanczos_equals_lanczos_per_column():
+    # the s recurrences run in lockstep (one block product per step) are each the
+    # single-vector Lanczos of their own probe
+    n, t = 150, 12
+    X = inputs.points(n, 3, "uniform", seed=17)
+    M = kernels.kernel_matrix(X, kernels.MATERN52, 0.3, 1.0, 1e-2)
+    F = precond.factors(*precond.build(M, rademacher_block(2, n, 10), 2, 1e-2))
+    B = precond.operator_B(M, F)
+    Z = rademacher_block(11, n, 5)
+    tri = estimator.lanczos_block(lambda W: B @ W, Z, t)
+    for c in range(Z.shape[1]):
+        a, bt, _ = estimator.lanczos(B, Z[:, c], t)
+        np.testing.assert_allclose(tri[c][0], a, rtol=1e-12)
+        np.testing.assert_allclose(tri[c][1], bt, rtol=1e-11)
+
+
+@pytest.mark.parametrize("k", coeffs.ORDERS)
+def test_block_lanczos_with_full_t_equals_direct_solves(k):
+    # t = n: the Krylov space is the whole space, so Algorithm 1 equals the converged
+    # estimator (dense shifted solves), here with B given only as a product
+    n = 48
+    X = inputs.points(n, 2, "uniform", seed=18)
+    M = kernels.kernel_matrix(X, kernels.RBF, 0.3, 1.0, 1e-1)
+    F = precond.factors(*precond.build(M, rademacher_block(2, n, 6), 1, 1e-1))
+    B = precond.operator_B(M, F)
+    Z = rademacher_block(12, n, 4)
+    e1, p1, _, _ = estimator.estimate_lanczos_block(lambda W: B @ W, F["logdet_P"], Z, k, n)
+    e2, p2, _ = estimator.estimate_converged(B, F["logdet_P"], Z, k)
+    np.testing.assert_allclose(p1, p2, rtol=1e-9)
+    assert e1 == pytest.approx(e2, rel=1e-11)
+
+
+def test_matrix_free_algorithm1_equals_dense_algorithm1():
+    # the same literal Algorithm 1 on B = L^-1 M L^-T applied matrix-free (kz_matfree)
+    # and on the dense B, with the SLQ forms of the same tridiagonals
+    n, t, ell, nu = 400, 10, 0.2, 1e-2
+    X = inputs.points(n, 4, "uniform", seed=19)
+    M = kernels.kernel_matrix(X, kernels.MATERN52, ell, 1.0, nu)
+    F = precond.factors(*precond.build(M, rademacher_block(2, n, 16), 1, nu))
+    B = precond.operator_B(M, F)
+    Z = rademacher_block(13, n, 6)
+    apply = precond.operator_B_apply(lambda V: kernels.kz_matfree(X, V, kernels.MATERN52, ell, 1.0, nu), F)
+    e_mf, p_mf, _, tri = estimator.estimate_lanczos_block(apply, F["logdet_P"], Z, 3, t)
+    e_d, p_d, _ = estimator.estimate_lanczos(B, F["logdet_P"], Z, 3, t)
+    np.testing.assert_allclose(p_mf, p_d, rtol=1e-10)
+    slq_mf = [estimator.slq_form(a, bt, float(Z[:, i] @ Z[:, i])) for i, (a, bt) in enumerate(tri)]
+    _, slq_d = estimator.estimate_slq(B, F["logdet_P"], Z, t)
+    np.testing.assert_allclose(slq_mf, slq_d, rtol=1e-10)
+
+
+def test_multishift_iterates_at_fixed_t_are_cg_iterates_of_each_shifted_system():
+    # After t steps (long before convergence) the multi-shift iterate of shift delta is
+    # the t-th plain CG iterate of (seed + delta I) x = z from x_0 = 0 (the Krylov space
+    # of z is shift-invariant), here from scipy's CG; its residual is what the residual
+    # check reports.
+    from scipy.sparse.linalg import cg
+    n, t = 200, 5
+    X = inputs.points(n, 2, "uniform", seed=20)
+    M = kernels.kernel_matrix(X, kernels.MATERN52, 0.2, 1.0, 1e-2)
+    F = precond.factors(*precond.build(M, rademacher_block(2, n, 8), 1, 1e-2))
+    B = precond.operator_B(M, F)
+    z = rademacher_block(14, n, 1)[:, 0]
+    _, _, sigma = coeffs.rk_coeffs(3)
+    seed = B + sigma[0] * np.eye(n)
+    xs = estimator.multishift_cg(seed, z, sigma - sigma[0], t)
+    for j, sj in enumerate(sigma):
+        ref, _ = cg(B + sj * np.eye(n), z, x0=np.zeros(n), rtol=0.0, atol=0.0, maxiter=t)
+        np.testing.assert_allclose(xs[j], ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
+        # not yet solved: the residual is far above rounding
+        assert np.linalg.norm(z - (B + sj * np.eye(n)) @ xs[j]) > 1e-4 * np.linalg.norm(z)

@@ -61,3 +61,13 @@ def test_kernel_matrix_is_spd_and_rows_match(kind):
     rows = np.array([0, 7, 128, 299])
     np.testing.assert_allclose(kernels.kz_rows(X, V, rows, kind, 0.2, 1.0, 1e-3), (M @ V)[rows],
                                rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", [kernels.RBF, kernels.MATERN52])
+def test_matrix_free_product_equals_dense_product(kind):
+    # every row of (K + noise I) V without forming K, over ragged row ranges on 3 threads
+    X = inputs.points(250, 4, "uniform", seed=6)
+    V = inputs.gaussian(250, 7, seed=10)
+    M = kernels.kernel_matrix(X, kind, 0.15, 1.3, 2e-2)
+    got = kernels.kz_matfree(X, V, kind, 0.15, 1.3, 2e-2, rows_per_task=7, threads=3)
+    np.testing.assert_allclose(got, M @ V, rtol=1e-12, atol=1e-12)

@@ -51,7 +51,7 @@ MUTANTS = [
       "test_oracle_estimator::test_hutchinson_exact_on_diagonal", 3, id="shift-sign"),
     P("oracle.estimator", "den = diag[i] - lower[i - 1] * cp[i - 1]", "den = diag[i] - lower[i - 1] * cp[i]",
       "test_oracle_estimator::test_thomas_matches_dense_solve", id="thomas-index"),
-    P("oracle.estimator", "q[i, j] = vn * w[0]", "q[i, j] = w[0]",
+    P("oracle.estimator", "out[j] = vn * w[0]", "out[j] = w[0]",
       "test_oracle_estimator::test_lanczos_reproduces_B_and_full_t_equals_direct", id="lanczos-dropped-norm"),
     P("oracle.estimator", "alpha[k] = q @ w", "alpha[k] = w @ w",
       "test_oracle_estimator::test_lanczos_reproduces_B_and_full_t_equals_direct", id="lanczos-diagonal"),
@@ -67,6 +67,10 @@ MUTANTS = [
       "test_oracle_estimator::test_multishift_cg_equals_direct_shifted_solves", id="multishift-zeta-sign"),
     P("oracle.estimator", "(b * (zeta_next / zeta) ** 2)", "(b * (zeta_next / zeta))",
       "test_oracle_estimator::test_multishift_cg_equals_direct_shifted_solves", id="multishift-beta-square"),
+    P("oracle.estimator", "alpha[c, k] = cur[:, c] @ w", "alpha[c, k] = w @ w",
+      "test_oracle_estimator::test_block_lanczos_equals_lanczos_per_column", id="block-lanczos-diagonal"),
+    P("oracle.estimator", "cur[:, c] = w / beta[c, k]", "cur[:, c] = w",
+      "test_oracle_estimator::test_block_lanczos_with_full_t_equals_direct_solves", 3, id="block-lanczos-normalisation"),
     # kernels (Section 3, Rasmussen & Williams forms)
     P("oracle.kernels", "(1.0 + u + u * u / 3.0)", "(1.0 + u + u * u / 2.0)",
       "test_oracle_kernels::test_matern52_equals_general_matern_bessel_form", id="matern-polynomial"),
@@ -78,6 +82,8 @@ MUTANTS = [
       "test_oracle_kernels::test_kernel_matrix_is_spd_and_rows_match", 0, id="dropped-noise"),
     P("oracle.kernels", "out += noise * V[rows]", "out += 0.0 * V[rows]",
       "test_oracle_kernels::test_kernel_matrix_is_spd_and_rows_match", 1, id="matrix-free-dropped-noise"),
+    P("oracle.kernels", "rows = np.arange(i0, min(n, i0 + rows_per_task))", "rows = np.arange(i0, min(n, i0 + rows_per_task - 1))",
+      "test_oracle_kernels::test_matrix_free_product_equals_dense_product", 1, id="matrix-free-row-range"),
     # preconditioner (Section 2, Appendix)
     P("oracle.precond", 'W = V + F["Q"] @ (F["Cinv"].T @ T - T)', 'W = V + F["Q"] @ (F["Cinv"] @ T - T)',
       "test_oracle_precond::test_split_factor_inverts_P", id="LinvT-transposed-core"),
@@ -89,6 +95,8 @@ MUTANTS = [
       "test_oracle_precond::test_rsvd_top_eigenvalues_on_kernel_matrix", id="residual-diagonal"),
     P("oracle.precond", "C = Q.T @ matmul(Q)", "C = Q.T @ Q",
       "test_oracle_precond::test_rsvd_recovers_exact_low_rank_plus_diagonal", id="rsvd-core"),
+    P("oracle.precond", "apply_Linv(F, matmul(apply_LinvT(F, V)))", "apply_LinvT(F, matmul(apply_Linv(F, V)))",
+      "test_oracle_precond::test_matrix_free_B_equals_dense_B", id="matrix-free-B-order"),
     # gradients (Section 3)
     P("oracle.gradient", "g[a] += -c[j] * np.sum(Y * (dM @ Y)) / s", "g[a] += c[j] * np.sum(Y * (dM @ Y)) / s",
       "test_oracle_gradient::test_estimator_gradient_matches_fd_with_frozen_P", 0, id="adjoint-sign"),

@@ -114,3 +114,13 @@ def test_rank_one_build_is_the_appendix_rank_one_preconditioner():
     np.testing.assert_allclose(A[:, 0] @ A[:, 0], lam[-1], rtol=1e-10)
     np.testing.assert_allclose(np.abs(A[:, 0]) / np.sqrt(lam[-1]), np.abs(v), atol=1e-8)
     np.testing.assert_allclose(D, np.maximum(np.diag(M - lam[-1] * np.outer(v, v)), 1e-2), rtol=1e-8)
+
+
+def test_matrix_free_B_equals_dense_B():
+    n = 120
+    X = inputs.points(n, 3, "uniform", seed=21)
+    M = kernels.kernel_matrix(X, kernels.RBF, 0.25, 1.0, 1e-2)
+    F = precond.factors(*precond.build(M, rademacher_block(2, n, 9), 1, 1e-2))
+    V = inputs.gaussian(n, 4, seed=22)
+    got = precond.operator_B_apply(lambda W: M @ W, F)(V)
+    np.testing.assert_allclose(got, precond.operator_B(M, F) @ V, rtol=1e-11, atol=1e-11)
