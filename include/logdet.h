@@ -104,7 +104,12 @@ typedef struct {
                                 diagonal > 0) of the Gaussian block of those columns, each
                                 column scaled by the norm of Gaussian column 2^30 + its
                                 index (a chi_n draw); device-drawn only */
-    int32_t reserved;
+    int32_t probe_col0;      /* >= 0: stream column of this call's first device-drawn probe
+                                (probe j uses column probe_col0 + j of the generator above;
+                                0 for a whole estimate).  The probes of one estimate can so
+                                be split over several calls or processes, each running the
+                                same P and its own columns; ld_combine joins their per-probe
+                                brackets into the estimate (Algorithm 1's output) */
 } ld_options;
 
 typedef struct {
@@ -115,7 +120,12 @@ typedef struct {
     int32_t iters;        /* max CG steps over the probe blocks */
     int32_t converged;    /* 1 if every column met rel_tol (or fixed_iters ran) */
     double max_resid[5];  /* residual check: max_i ||z_i - (B + sigma_j) x_ij|| / ||z_i||,
-                             fp64 norms; entries beyond the order are 0 */
+                             fp64 norms; entries beyond the order are 0.  The product
+                             B x_ij inside it runs in the estimate's precision: fp64
+                             in LD_FP64; in the other precisions its relative error
+                             (~1e-6 for LD_F16X3_TC and LD_FP32, ~1e-3 for LD_F16_TC,
+                             ~1e-2 for LD_BF16_TC) times |B x| / |z| is the floor
+                             below which a residual is not resolved */
     double final_rel_resid; /* max_i ||r_i|| / ||z_i|| of the seed system at exit */
     double slq_logdet;    /* stochastic Lanczos quadrature (Ubaru et al., Section 3's
                              comparison method) from the same Lanczos tridiagonals:
@@ -161,9 +171,12 @@ int ld_kz(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
  * __device__ array of ld_kz_static_capacity() bytes (32 MiB) that every GPU
  * loading the library keeps until process exit; sizes whose scratch
  * (ld_kz_workspace_size) exceeds it return LD_ERR_WORKSPACE.  The first call on
- * a device looks up the array's address there (make it before any stream
- * capture).  All calls share the array: calls that overlap on the GPU race.
- * Arguments and results are those of ld_kz. */
+ * a device looks up the array's address there (cudaGetSymbolAddress): make that
+ * one-time first call before any stream capture begins.  Like ld_kz, a call in
+ * a tensor-core precision synchronises `stream` before returning; in FP64 and
+ * FP32 the work stays queued on it.  All calls share the array: calls that
+ * overlap on the GPU race.  Arguments, size limits (d <= 32; d <= 8 in the
+ * tensor-core precisions) and results are those of ld_kz. */
 size_t ld_kz_static_capacity(void);
 int ld_kz_static(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
                  const void *V_dev, void *W_dev, int32_t c, int32_t precision,
@@ -183,9 +196,9 @@ int ld_kz_dl(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
  * product.  LD_FP64 / LD_FP32: CUDA-core GEMM, asynchronous on the stream.
  * Tensor-core precisions (LD_BF16_TC, LD_F16_TC, LD_F16X3_TC; c <= 4096): M is
  * rounded (or split hi/lo) like the computed kernel values of ld_kz after
- * scaling by the power of two that brings max_i |M_ii| below 1, so M must be
- * positive semidefinite (|M_ij| <= max_i M_ii, true of every K + noise I; an
- * entry beyond that may overflow fp16 and make W non-finite); the call
+ * scaling by the power of two that brings max_i |M_ii| into [2^14, 2^15), so M
+ * must be positive semidefinite (|M_ij| <= max_i M_ii, true of every K + noise I;
+ * an entry beyond about twice that overflows fp16 and makes W non-finite); the call
  * allocates its scratch (the fp16/bf16 image of V), synchronises the stream and
  * returns LD_ERR_DEVICE_TIMEOUT if a device-side wait gave up. */
 size_t ld_dense_bytes(int64_t n, int32_t precision);
@@ -269,6 +282,15 @@ int logdet_estimate(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
                     const ld_precond *P, const ld_options *opt,
                     const int8_t *probes_dev, double *per_probe_host,
                     void *ws, size_t ws_bytes, void *stream, ld_result *out);
+
+/* Algorithm 1's output from per-probe brackets (host only, no device work):
+ * logdet = logdet_P + trace_est, trace_est = (1/S) sum_i bracket_i (summed in
+ * index order), std_err = sample std of the brackets / sqrt(S); every other
+ * field of *out is 0 except logdet_P.  For an estimate whose probe blocks ran
+ * in several calls or processes (each with the same P, its own probe_col0 and
+ * per_probe_host), the brackets concatenated in probe order give the same
+ * value as one call over all probes.  S >= 1; NULL pointers: LD_ERR_INVALID. */
+int ld_combine(const double *brackets_host, int32_t num_probes, double logdet_P, ld_result *out);
 
 /* Gradient of the estimator with P and the probes held fixed:
  *   d/dtheta = (1/s) sum_i sum_j (-c_j) y_ij^T (dM/dtheta) y_ij,

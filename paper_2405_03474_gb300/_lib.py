@@ -50,7 +50,7 @@ class LdOptions(ctypes.Structure):
     _fields_ = [("order", c_int32), ("num_probes", c_int32), ("probes_per_block", c_int32),
                 ("max_iters", c_int32), ("fixed_iters", c_int32), ("precision", c_int32),
                 ("residual_check", c_int32), ("dense", c_int32), ("seed", c_uint64),
-                ("rel_tol", c_double), ("probe_kind", c_int32), ("reserved", c_int32)]
+                ("rel_tol", c_double), ("probe_kind", c_int32), ("probe_col0", c_int32)]
 
 
 class LdResult(ctypes.Structure):
@@ -87,6 +87,7 @@ _SIGS = {
     "precond_free": (None, [_P]),
     "logdet_workspace_size": (c_size_t, [c_int64, c_int32, _P, _P]),
     "logdet_estimate": (c_int32, [_P, c_int64, c_int32, LdKernel, _P, _P, _P, _P, _P, c_size_t, _P, _P]),
+    "ld_combine": (c_int32, [_P, c_int32, c_double, _P]),
     "logdet_grad": (c_int32, [_P, c_int64, c_int32, LdKernel, _P, _P, _P, _P, c_size_t, _P, _P, _P]),
     "ld_launch_count": (c_int64, []),
     "ld_selftest_wait_timeout": (c_int32, [c_int64, _P]),

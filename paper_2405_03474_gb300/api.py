@@ -244,11 +244,22 @@ class Precond:
 
 
 def make_options(order=3, num_probes=16, probes_per_block=None, max_iters=1000, fixed_iters=0,
-                 precision="fp32", residual_check=False, seed=1, rel_tol=1e-6, dense=False, probe_kind="rademacher"):
+                 precision="fp32", residual_check=False, seed=1, rel_tol=1e-6, dense=False, probe_kind="rademacher",
+                 probe_col0=0):
     kind = {"rademacher": 0, "gaussian": 1, "orthogonal": 2}[probe_kind] if isinstance(probe_kind, str) else int(probe_kind)
     return LdOptions(int(order), int(num_probes), int(probes_per_block or num_probes), int(max_iters),
                      int(fixed_iters), _prec(precision), int(bool(residual_check)), int(bool(dense)), int(seed),
-                     float(rel_tol), kind, 0)
+                     float(rel_tol), kind, int(probe_col0))
+
+
+def ld_combine(brackets, logdet_P):
+    """Algorithm 1's output (log det, trace, std-err) from per-probe brackets (host)."""
+    lib = _lib.load()
+    br = np.ascontiguousarray(brackets, dtype=np.float64)
+    res = LdResult()
+    check(lib.ld_combine(br.ctypes.data_as(ctypes.c_void_p), int(br.size), float(logdet_P), ctypes.byref(res)),
+          "ld_combine")
+    return {"logdet": res.logdet, "logdet_P": res.logdet_P, "trace_est": res.trace_est, "std_err": res.std_err}
 
 
 def _result_dict(res, status, per_probe=None):

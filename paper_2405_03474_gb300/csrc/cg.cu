@@ -477,11 +477,11 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
                 gather_probes_kernel<T><<<nb(ns), 256, 0, st>>>(probes, n, o.num_probes, blk * s, s, b.Z);
                 LD_TRY(check_launch("gather_probes"));
             } else if (o.probe_kind == 1) {
-                LD_TRY(gaussian<T>(o.seed, n, s, blk * s, b.Z, st));
+                LD_TRY(gaussian<T>(o.seed, n, s, o.probe_col0 + blk * s, b.Z, st));
             } else if (o.probe_kind == 2) {
-                LD_TRY(orthogonal_probes<T>(o.seed, n, s, blk * s, b.Z, b.Bp, b.y, b.w, a, st));
+                LD_TRY(orthogonal_probes<T>(o.seed, n, s, o.probe_col0 + blk * s, b.Z, b.Bp, b.y, b.w, a, st));
             } else {
-                LD_TRY(rademacher(o.seed, n, s, blk * s, b.Zi8, st));
+                LD_TRY(rademacher(o.seed, n, s, o.probe_col0 + blk * s, b.Zi8, st));
                 LD_TRY(int8_to<T>(b.Zi8, b.Z, (int64_t)ns, st));
             }
             LD_CHECK_CUDA(cudaMemcpyAsync(b.r, b.Z, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
@@ -609,8 +609,9 @@ int validate(const double *X, int64_t n, int d, const ld_kernel &k, const ld_pre
     LD_REQUIRE(o->dense == 0 || o->dense == 1, "dense must be 0 or 1");
     LD_REQUIRE(o->probe_kind >= 0 && o->probe_kind <= 2,
                "probe_kind must be 0 (Rademacher), 1 (Gaussian) or 2 (normal orthogonal)");
-    LD_REQUIRE(o->probe_kind != 2 || (o->probes_per_block <= n && o->num_probes < ORF_NORM_COL0),
-               "orthogonal probes need probes_per_block <= n");
+    LD_REQUIRE(o->probe_col0 >= 0 && (int64_t)o->probe_col0 + o->num_probes < ORF_NORM_COL0,
+               "probe_col0 must be >= 0 with probe_col0 + num_probes < 2^30");
+    LD_REQUIRE(o->probe_kind != 2 || o->probes_per_block <= n, "orthogonal probes need probes_per_block <= n");
     LD_REQUIRE(o->dense == 0 || n <= (int64_t)1 << 18, "dense mode keeps n*n words: n <= 262144");
     if (P) {
         LD_REQUIRE(P->n == n, "preconditioner built for n = %lld, not %lld", (long long)P->n, (long long)n);
@@ -622,20 +623,26 @@ int validate(const double *X, int64_t n, int d, const ld_kernel &k, const ld_pre
     return LD_OK;
 }
 
-void fill_result(const RunOut &r, const ld_precond *P, const ld_options &o, ld_result *out,
-                 double *per_probe) {
+// Algorithm 1's output: log det P + the Hutchinson mean of the per-probe brackets
+// (summed in index order), and the standard error of that mean.
+void combine_brackets(const double *br, int S, double ldP, ld_result *out) {
     double mean = 0.0;
-    for (double v : r.brackets) mean += v;
-    const int S = (int)r.brackets.size();
+    for (int i = 0; i < S; ++i) mean += br[i];
     mean /= S;
     double var = 0.0;
-    for (double v : r.brackets) var += (v - mean) * (v - mean);
+    for (int i = 0; i < S; ++i) var += (br[i] - mean) * (br[i] - mean);
     var = S > 1 ? var / (S - 1) : 0.0;
-    const double ldP = P ? P->logdet_P : 0.0;
     out->logdet = ldP + mean;
     out->logdet_P = ldP;
     out->trace_est = mean;
     out->std_err = sqrt(var / S);
+}
+
+void fill_result(const RunOut &r, const ld_precond *P, const ld_options &o, ld_result *out,
+                 double *per_probe) {
+    const int S = (int)r.brackets.size();
+    const double ldP = P ? P->logdet_P : 0.0;
+    combine_brackets(r.brackets.data(), S, ldP, out);
     out->iters = r.iters;
     out->converged = r.converged ? 1 : 0;
     for (int j = 0; j < 5; ++j) out->max_resid[j] = r.max_resid[j];
@@ -695,6 +702,15 @@ int logdet_estimate(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, c
                   opt->max_iters, r.final_rel);
         return LD_ERR_NOT_CONVERGED;
     }
+    return LD_OK;
+}
+
+int ld_combine(const double *brackets_host, int32_t num_probes, double logdet_P, ld_result *out) {
+    clear_error();
+    LD_REQUIRE(brackets_host != nullptr && out != nullptr, "ld_combine: NULL pointer");
+    LD_REQUIRE(num_probes >= 1, "ld_combine: need at least one probe");
+    *out = ld_result{};
+    combine_brackets(brackets_host, num_probes, logdet_P, out);
     return LD_OK;
 }
 
