@@ -470,7 +470,7 @@ __global__ void sym_point_tiles_kernel(const float *Xs, int64_t n, int d, float 
     const int rem = (int)(idx % per);
     const int a = rem / BR, jj = rem % BR;
     const int64_t i = t * BR + jj;
-    Xp[idx] = i < n ? Xs[i * d + a] * factor : 1e18f;
+    Xp[idx] = i < n ? Xs[i * d + a] * factor : PAD_COORD;
 }
 
 // V operand image per 128-point tile: SN columns x 128 K values, canonical K-major
@@ -531,7 +531,9 @@ __global__ void sym_colscale_kernel(const float *part, int nb, int sn, float *sc
     for (int b = 0; b < nb; ++b) m = fmaxf(m, part[(size_t)b * sn + col]);
     int e = 0;
     if (m > 0.f) frexpf(m, &e);
-    const float s = ldexpf(1.0f, -e);
+    // max |V_col| s in [KSCALE / 2, KSCALE): the lo part of the split stays out of
+    // fp16 subnormals (as for the kernel values, tc_common.cuh)
+    const float s = ldexpf(1.0f, KSCALE_LOG2 - e);
     scale[col] = s;
     colinv[col] = 1.0f / s;
 }
@@ -645,7 +647,7 @@ int kz_sym(const float *Xs, int64_t n, int d, int kind, double variance, double 
         const int tcols = nprod == 3 ? 8 * sn : 3 * sn;
         p.ncols_tmem = tcols <= 32 ? 32 : (tcols <= 64 ? 64 : (tcols <= 128 ? 128 : (tcols <= 256 ? 256 : 512)));
         p.vec_ok = (reinterpret_cast<uintptr_t>(W) % 16 == 0) && ((c * 4) % 16 == 0);
-        p.variance = (float)variance;
+        p.variance = (float)variance * KSCALE_INV;  // kernel values carry KSCALE
         p.noise = (float)noise;
         p.err = err;
         const SymLayout L = make_sym_layout(sn, d, nprod, sym_stages(sn, d, nprod));

@@ -20,14 +20,16 @@
 //
 // Precisions: LD_F16_TC (K, V in fp16), LD_BF16_TC (bf16), LD_F16X3_TC
 // (K = Kh + Kl, V = Vh + Vl in fp16; D += Kh Vh + Kh Vl + Kl Vh).  V columns are
-// scaled by powers of two so |V| <= 1 before rounding; K is computed with unit
-// variance and the variance is applied in the epilogue.
+// scaled by powers of two so max |V_col| lies in [KSCALE / 2, KSCALE) before
+// rounding; K is computed with unit
+// variance times KSCALE (tc_common.cuh) and variance / KSCALE is applied in the
+// epilogue.
 //
 // The same pipeline serves a stored dense M = K + noise I (FROMM): the eval warps
 // then read 4 x 8 values each of every 128 x 64 tile of M from HBM (streaming
 // loads, three tiles in flight per thread, 8 rows x 128 bytes per warp load),
-// scale them by a power of two that brings max |M_ii| below 1 and round/split
-// them exactly as computed values; the producer streams only the operand image
+// scale them by a power of two that brings max |M_ii| into [KSCALE / 2, KSCALE)
+// and round/split them exactly as computed values; the producer streams only the operand image
 // of V.  One pass reads M once, so the product is bound by HBM instead of the
 // FP32 pipes of the SIMT GEMM.
 #include <cuda_bf16.h>
@@ -461,7 +463,7 @@ __global__ void __launch_bounds__(NTHREADS, FROMM ? 1 : 2) kz_tc_kernel(TcParams
 
 // Point tiles for the kernel: per 64-point tile, coordinate-major (d x 64) so a
 // pair of neighbouring points is one 8-byte load; coordinates scaled once more
-// by `factor`; points past n are placed at 1e18 so every kernel value with them
+// by `factor`; points past n are placed at PAD_COORD so every kernel value with them
 // is exactly 0 (2^-x underflows) and no bounds test is needed.
 __global__ void point_tiles_kernel(const float *Xs, int64_t n, int d, float factor, int64_t ntiles_alloc,
                                    float *Xp) {
@@ -472,7 +474,7 @@ __global__ void point_tiles_kernel(const float *Xs, int64_t n, int d, float fact
     const int rem = (int)(idx % per);
     const int a = rem / TJ, jj = rem % TJ;
     const int64_t i = t * TJ + jj;
-    Xp[idx] = i < n ? Xs[i * d + a] * factor : 1e18f;
+    Xp[idx] = i < n ? Xs[i * d + a] * factor : PAD_COORD;
 }
 
 // ------------------------------------------------------------ prep kernels
@@ -494,19 +496,23 @@ __global__ void colscale_kernel(const float *part, int nb, int N, float *scale, 
     if (col >= N) return;
     float m = 0.f;
     for (int b = 0; b < nb; ++b) m = fmaxf(m, part[(size_t)b * N + col]);
-    // power of two with m * s <= 1 (exact rescaling)
+    // power of two (exact rescaling)
     int e = 0;
     if (m > 0.f) {
         frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
     }
-    const float s = ldexpf(1.0f, -e);
+    // max |V_col| s in [KSCALE / 2, KSCALE): the lo part of the split stays out of
+    // fp16 subnormals (as for the kernel values, tc_common.cuh)
+    const float s = ldexpf(1.0f, KSCALE_LOG2 - e);
     scale[col] = s;
     colinv[col] = 1.0f / s;
 }
 
-// Scale of a stored M: the power of two s with max_i |M_ii| s < 1 (s = 1 when the
-// diagonal is zero or not finite); for a positive semidefinite M every entry
-// satisfies |M_ij| <= max_i M_ii, so every scaled entry lies in [-1, 1].
+// Scale of a stored M: the power of two s with max_i |M_ii| s in [KSCALE / 2, KSCALE)
+// (s = KSCALE when the diagonal is zero or not finite); for a positive semidefinite M
+// every entry satisfies |M_ij| <= max_i M_ii, so every scaled entry lies in
+// [-KSCALE, KSCALE], inside fp16's range with full precision down to ~1e-9 max M_ii
+// (as for the computed kernel values).
 __global__ void diag_scale_kernel(const float *M, int64_t n, float *mscale) {
     __shared__ float red[256];
     float m = 0.f;
@@ -521,8 +527,8 @@ __global__ void diag_scale_kernel(const float *M, int64_t n, float *mscale) {
         const float mx = red[0];
         int e = 0;
         if (mx > 0.f && isfinite(mx)) frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
-        mscale[0] = ldexpf(1.0f, -e);
-        mscale[1] = ldexpf(1.0f, e);
+        mscale[0] = ldexpf(1.0f, KSCALE_LOG2 - e);
+        mscale[1] = ldexpf(1.0f, e - KSCALE_LOG2);
     }
 }
 
@@ -714,7 +720,7 @@ int kz_tc(const float *Xs, int64_t n, int d, int kind, double variance, double n
             const int tcols = (nprod == 3 && N <= DRAIN_MAX_N) ? 2 * N : N;  // ping-pong buffers
             p.ncols_tmem = tmem_cols(tcols);
             p.ntiles = (int)ntiles;
-            p.variance = (float)variance;
+            p.variance = (float)variance * KSCALE_INV;  // kernel values carry KSCALE
             p.noise = (float)noise;
             p.err = err;
             p.M = nullptr;

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
             for (int a = 0; a < 8; ++a) {
                 const int64_t i = row0 + lane + 32 * k;
                 const float v = (a < dd && i < p.n) ? -p.Xp[(size_t)(i / WJ) * WJ * dd + a * WJ + (i % WJ)]
-                                                    : (a < dd ? -1e18f : 0.f);
+                                                    : (a < dd ? -PAD_COORD : 0.f);
                 xr[k][a] = make_float2(v, v);
             }
         bool ok = true;
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(WTHREADS, 1) kz_wide_kernel(WideParams p, Wide
     if (threadIdx.x == 0 && *s_err) atomicOr(p.err, *s_err);
 }
 
-// 64-point tiles, coordinate-major, log2 e folded in, far padding (points past n at 1e18)
+// 64-point tiles, coordinate-major, log2 e folded in, far padding (points past n at PAD_COORD)
 __global__ void wide_point_tiles_kernel(const float *Xs, int64_t n, int d, float factor, int64_t ntiles,
                                         float *Xp) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -328,7 +328,7 @@ __global__ void wide_point_tiles_kernel(const float *Xs, int64_t n, int d, float
     const int rem = (int)(idx % per);
     const int a = rem / WJ, jj = rem % WJ;
     const int64_t i = t * WJ + jj;
-    Xp[idx] = i < n ? Xs[i * d + a] * factor : 1e18f;
+    Xp[idx] = i < n ? Xs[i * d + a] * factor : PAD_COORD;
 }
 
 __global__ void wide_colmax_kernel(const float *V, int64_t n, int c, int N, float *part) {
@@ -349,7 +349,9 @@ __global__ void wide_colscale_kernel(const float *part, int nb, int N, float *sc
     for (int b = 0; b < nb; ++b) m = fmaxf(m, part[(size_t)b * N + col]);
     int e = 0;
     if (m > 0.f) frexpf(m, &e);
-    const float s = ldexpf(1.0f, -e);
+    // max |V_col| s in [KSCALE / 2, KSCALE): the lo part of the split stays out of
+    // fp16 subnormals (as for the kernel values, tc_common.cuh)
+    const float s = ldexpf(1.0f, KSCALE_LOG2 - e);
     scale[col] = s;
     colinv[col] = 1.0f / s;
 }
@@ -484,7 +486,7 @@ int kz_wide(const float *Xs, int64_t n, int d, int kind, double variance, double
         p.nchunks = (int)((ntiles + WCHUNK - 1) / WCHUNK);
         p.vec_ok = (reinterpret_cast<uintptr_t>(W) % 16 == 0) && (c % 4 == 0);
         if (p.nchunks > 1) LD_CHECK_CUDA(cudaMemsetAsync(W, 0, sizeof(float) * (size_t)n * c, st));
-        p.variance = (float)variance;
+        p.variance = (float)variance * KSCALE_INV;  // kernel values carry KSCALE
         p.noise = (float)noise;
         p.err = err;
         const WideLayout L = make_wide_layout(N, d, wide_stages(N, d));

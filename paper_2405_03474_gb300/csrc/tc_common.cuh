@@ -169,9 +169,25 @@ __device__ __forceinline__ float mufu_sqrt(float x) {
     return r;
 }
 
-// Unit-variance kernel values of two pairs from their squared scaled distances.
-// The coordinates carry an extra log2(e) factor (Matern) or sqrt(log2 e) (RBF),
-// so the exponential is a bare 2^-x:
+// Kernel values are produced scaled by KSCALE = 2^15 (the products' epilogues multiply
+// by KSCALE_INV with the variance).  Unit-variance values lie in [0, 1]; scaled they
+// lie in [0, 2^15], inside fp16's range, and fp16 keeps its full 11 significant bits
+// down to k = 2^-14 / 2^15 ~ 1.9e-9 instead of 6.1e-5, so the hi/lo split represents
+// k to ~2^-21 relative (and to ~1e-12 absolute below that) rather than losing the lo
+// part of every k < 0.06 to fp16 subnormals.  Powers of two: the scaling is exact.
+constexpr int KSCALE_LOG2 = 15;
+constexpr float KSCALE = 32768.0f;
+constexpr float KSCALE_INV = 1.0f / 32768.0f;
+
+// Coordinate of the padding points past n: every kernel value with them is exactly
+// 0 (2^-x underflows), and squared distances to them (< 1e26 for the at most 8
+// dimensions, coordinates of real points far below 1e12) keep the scaled Matern
+// polynomial finite in fp32.
+constexpr float PAD_COORD = 1e12f;
+
+// KSCALE times the unit-variance kernel values of two pairs from their squared scaled
+// distances.  The coordinates carry an extra log2(e) factor (Matern) or sqrt(log2 e)
+// (RBF), so the exponential is a bare 2^-x:
 //   Matern: u' = u log2 e,  k = (1 + u' ln2 + u'^2 ln2^2 / 3) 2^-u'
 //   RBF:    u2' = u2 log2 e, k = 2^-u2'
 constexpr float LN2 = 0.69314718055994531f;
@@ -179,11 +195,14 @@ constexpr float LN2SQ_3 = 0.16015100463940035f;  // (ln 2)^2 / 3
 
 template <int KIND>
 __device__ __forceinline__ float2 kval2(float2 u2) {
-    if (KIND == LD_RBF) return make_float2(mufu_ex2_neg(u2.x), mufu_ex2_neg(u2.y));
+    if (KIND == LD_RBF)
+        return __fmul2_rn(make_float2(mufu_ex2_neg(u2.x), mufu_ex2_neg(u2.y)), make_float2(KSCALE, KSCALE));
     const float2 u = make_float2(mufu_sqrt(u2.x), mufu_sqrt(u2.y));
     const float2 e = make_float2(mufu_ex2_neg(u.x), mufu_ex2_neg(u.y));
-    const float2 poly = __ffma2_rn(__ffma2_rn(u, make_float2(LN2SQ_3, LN2SQ_3), make_float2(LN2, LN2)), u,
-                                   make_float2(1.f, 1.f));
+    // the polynomial's coefficients carry KSCALE
+    const float2 poly = __ffma2_rn(__ffma2_rn(u, make_float2(LN2SQ_3 * KSCALE, LN2SQ_3 * KSCALE),
+                                              make_float2(LN2 * KSCALE, LN2 * KSCALE)),
+                                   u, make_float2(KSCALE, KSCALE));
     return __fmul2_rn(poly, e);
 }
 
