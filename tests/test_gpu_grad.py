@@ -4,7 +4,7 @@ central finite differences at n = 131072, and the torch.autograd.Function."""
 import numpy as np
 import pytest
 
-from gpu_util import cuda, host, relerr, torch
+from gpu_util import cuda, host, torch
 from oracle import gradient, kernels, precond
 from oracle.splitmix import rademacher_block
 from paper_2405_03474_gb300 import api, autograd, inputs

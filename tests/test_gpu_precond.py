@@ -2,12 +2,22 @@
 import numpy as np
 import pytest
 
-from gpu_util import cuda, host, relerr, torch
+from gpu_util import assert_elementwise, cuda, host, torch
 from oracle import kernels, precond
 from oracle.splitmix import rademacher_block
 from paper_2405_03474_gb300 import api, inputs
 
 pytestmark = pytest.mark.gpu
+
+
+def _apply_scales(F, V):
+    """Elementwise magnitude bounds of L^-1 V and L^-T V: the same products as
+    precond.apply_Linv / apply_LinvT with every factor replaced by its absolute value."""
+    Q, Ci, ds = np.abs(F["Q"]), np.abs(F["Cinv"] - np.eye(F["Cinv"].shape[0])), F["dinv_sqrt"]
+    W = ds[:, None] * np.abs(V)
+    s_inv = W + Q @ (Ci @ (Q.T @ W))
+    s_invT = ds[:, None] * (np.abs(V) + Q @ (Ci.T @ (Q.T @ np.abs(V))))
+    return s_inv, s_invT
 
 
 def _lowrank(n, r, seed):
@@ -28,8 +38,9 @@ def test_import_factor_and_apply(prec, tol):
     V = inputs.gaussian(n, c, seed=1)
     dt = torch.float64 if prec == "fp64" else torch.float32
     Vt = cuda(V, dt)
-    assert relerr(host(P.apply(Vt, transpose=False)), precond.apply_Linv(F, V)) < tol
-    assert relerr(host(P.apply(Vt, transpose=True)), precond.apply_LinvT(F, V)) < tol
+    s_inv, s_invT = _apply_scales(F, V)
+    assert_elementwise(host(P.apply(Vt, transpose=False)), precond.apply_Linv(F, V), s_inv, tol, "L^-1 V")
+    assert_elementwise(host(P.apply(Vt, transpose=True)), precond.apply_LinvT(F, V), s_invT, tol, "L^-T V")
     A2, D2, ld2 = P.export()
     np.testing.assert_allclose(D2, D, rtol=1e-15)
     np.testing.assert_allclose(A2 @ A2.T, A @ A.T, rtol=0, atol=(1e-10 if prec == "fp64" else 1e-4) * np.abs(A @ A.T).max())
@@ -90,3 +101,25 @@ def test_diagonal_and_plus_scaling_variants_match_oracle():
     np.testing.assert_array_equal(D, Do)
     assert np.abs(A @ A.T - Ao @ Ao.T).max() < 1e-9 * np.abs(Ao @ Ao.T).max()
     assert ldP == pytest.approx(precond.factors(Ao, Do)["logdet_P"], rel=1e-10)
+
+
+def test_build_with_fp16_sketch_matches_its_export_and_the_oracle():
+    # the bench builds P with the fp16 tensor-core sketch: the handle's log det P is that of
+    # the factors it exports (oracle determinant lemma), and close to the oracle's own build
+    # from the same Rademacher sketch (the fp16 products move the subspace slightly)
+    n, d, r, q, nu = 4000, 4, 64, 2, 1e-2
+    X = inputs.points(n, d, "uniform", seed=2)
+    k = api.Kernel(api.MATERN52, 0.2, 1.0, nu)
+    P = api.Precond.build(cuda(X), k, r, power_iters=q, seed=2, precision="f16_tc")
+    A, D, ldP = P.export()
+    F = precond.factors(A, D)
+    assert ldP == pytest.approx(F["logdet_P"], rel=1e-6)
+    M = kernels.kernel_matrix(X, api.MATERN52, 0.2, 1.0, nu)
+    Ao, Do = precond.build(M, rademacher_block(2, n, r), q, nu)
+    assert ldP == pytest.approx(precond.factors(Ao, Do)["logdet_P"], rel=2e-3)
+    # its applies are those of the exported factors
+    V = inputs.gaussian(n, 5, seed=3)
+    s_inv, s_invT = _apply_scales(F, V)
+    assert_elementwise(host(P.apply(cuda(V, torch.float32))), precond.apply_Linv(F, V), s_inv, 2e-5, "L^-1 V")
+    assert_elementwise(host(P.apply(cuda(V, torch.float32), transpose=True)), precond.apply_LinvT(F, V), s_invT,
+                       2e-5, "L^-T V")

@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from gpu_util import cuda, host, relerr, torch
+from gpu_util import assert_elementwise, cuda, host, torch
 from oracle import mlp
 from paper_2405_03474_gb300 import api
 
@@ -24,7 +24,8 @@ def test_loss_and_parameter_gradient_match_oracle():
     loss, g = S.loss_grad(cuda(X), cuda(y))
     lo, go, _ = mlp.loss_and_grads(flat.astype(np.float64), X.astype(np.float64), y.astype(np.float64))
     assert loss == pytest.approx(lo, rel=1e-5)
-    assert relerr(g, go) < 1e-5
+    # fp32 sums over the batch: each entry within 1e-5 of the largest gradient entry
+    assert_elementwise(g, go, np.full(go.shape, np.abs(go).max()), 1e-5, "parameter gradient")
 
 
 def test_inference_and_input_gradient_match_oracle():
@@ -34,8 +35,8 @@ def test_inference_and_input_gradient_match_oracle():
     out, dout = S.infer(cuda(X), want_grad=True)
     ref, _ = mlp.forward(flat.astype(np.float64), X.astype(np.float64))
     _, _, dX = mlp.loss_and_grads(flat.astype(np.float64), X.astype(np.float64), np.zeros(1000))
-    assert relerr(host(out), ref) < 1e-5
-    assert relerr(host(dout), dX) < 1e-5
+    assert_elementwise(host(out), ref, np.full(ref.shape, np.abs(ref).max()), 1e-5, "network output")
+    assert_elementwise(host(dout), dX, np.full(dX.shape, np.abs(dX).max()), 1e-5, "input gradient")
 
 
 def test_adam_steps_match_oracle():
