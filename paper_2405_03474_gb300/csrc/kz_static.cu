@@ -11,11 +11,14 @@
 // that array until the process exits.
 //
 // The array's device address is looked up once per device, with that device
-// current, the first time this entry point runs on it; that first call should
-// therefore come before any stream capture.  All calls share the one array and
-// it keeps the previous call's contents: the product rewrites everything it
-// reads and clears its error word itself, but two calls whose work overlaps on
-// the GPU (different streams, or host threads) race on the array.
+// current, the first time this entry point runs on it (cudaGetSymbolAddress);
+// make that first call on each device before any stream capture begins.  Like
+// ld_kz, a call in a tensor-core precision synchronises its stream before it
+// returns (it reads the product's error word); in FP64 and FP32 the work stays
+// queued on the stream.  All calls share the one array and it keeps the
+// previous call's contents: the product rewrites everything it reads and clears
+// its error word itself, but two calls whose work overlaps on the GPU
+// (different streams, or host threads) race on the array.
 #include <mutex>
 
 #include "common.cuh"
@@ -68,7 +71,9 @@ int ld_kz_static(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, cons
     clear_error();
     LD_REQUIRE(X_dev && V_dev && W_dev && n > 0 && c > 0, "ld_kz_static: bad pointers or sizes");
     LD_REQUIRE(V_dev != W_dev, "ld_kz_static: W must not alias V");
-    LD_REQUIRE(d >= 1 && d <= 8, "ld_kz_static: d must be in [1, 8]");
+    LD_REQUIRE(d >= 1 && d <= 32, "ld_kz_static: d must be in [1, 32]");
+    LD_REQUIRE(d <= 8 || precision == LD_FP64 || precision == LD_FP32,
+               "ld_kz_static: tensor-core precisions support d <= 8");
     LD_REQUIRE(c <= 4096, "ld_kz_static: at most 4096 columns");
     LD_REQUIRE(kern.lengthscale > 0 && kern.variance > 0 && kern.noise >= 0 &&
                    (kern.kind == LD_RBF || kern.kind == LD_MATERN52),
