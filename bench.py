@@ -37,6 +37,10 @@ UNIT = "estimates/s"
 # sqrt and one ex2; RBF 2d fp32 ops and one ex2.
 SMS, SM_MHZ_MAX, FP32_PER_CLK, EX2_PER_CLK, SQRT_PER_CLK = 152, 2070.0, 128, 32, 16
 
+# rows of the matrix-free oracle product sampled per host core, in both the
+# cpu_baseline leg and the --impl reference arm
+ROWS_PER_CORE = 4
+
 
 # DRAM traffic of one launch of the dominant kernel (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum, one pass, n = 2^20, 16 columns, hi/lo fp16: 1.02 GB read +
@@ -102,9 +106,23 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-precision-compare", action="store_true",
                     help="skip the one-launch-per-precision product comparison after the timed region")
+    ap.add_argument("--estimate-compare", default="fp32", metavar="PRECS",
+                    help="comma-separated precisions whose estimate is run once after the timed region with the "
+                         "same preconditioner and probes ('' to skip; fp64 imports the preconditioner's factors "
+                         "into an FP64 handle)")
     ap.add_argument("--kz-only", type=int, default=0, metavar="C",
                     help="profiling aid: run only the kernel product on C columns (2 warm-up + 1 launch)")
     return ap.parse_args()
+
+
+def config_of(args, w):
+    """The workload's configuration, the same in both arms' JSON lines."""
+    from paper_2405_03474_gb300 import inputs
+    return {"workload": WORKLOAD, "n": w["n"], "d": w["d"],
+            "kernel": "matern52" if w["kind"] == inputs.MATERN52 else "rbf", "lengthscale": w["lengthscale"],
+            "variance": w["variance"], "noise": w["noise"], "order": w["order"], "rank": w["rank"],
+            "power_iters": w["power_iters"], "probes": w["probes"], "lanczos_steps": args.t,
+            "residual_check": True, "l2": "flushed between steps (256 MiB write, outside step events)"}
 
 
 def workload(args):
@@ -172,7 +190,7 @@ class OraclePool:
             else:
                 os.environ[k] = v
 
-    def estimate_seconds(self, t_steps, rows_per_core=4):
+    def estimate_seconds(self, t_steps, rows_per_core=None):
         """Seconds the CPU oracle needs for one estimate of the workload,
         extrapolated from its matrix-free K V on a sample of rows (all cores in
         parallel): (q + 2) sketch products with `rank` columns, t CG products with
@@ -180,6 +198,7 @@ class OraclePool:
         w = self.w
         n = w["n"]
         per_pass = {}
+        rows_per_core = rows_per_core or ROWS_PER_CORE
         sample_rows = rows_per_core * self.cores
         import numpy as np
         stride = max(1, n // sample_rows)  # rows spread over the whole point set
@@ -355,6 +374,45 @@ def run_ours(args, rank, world, local_rank, pool):
     if rank != 0:
         return None
 
+    # The same estimate in other precisions, once each after the timed region: one
+    # preconditioner (built as in the timed step) and the same device-drawn probes, so
+    # the estimates differ only by the arithmetic of the products and CG; time by CUDA
+    # events around each call, relative difference from the timed precision's estimate.
+    estimate_compare = None
+    precs = [p_ for p_ in args.estimate_compare.split(",") if p_]
+    if precs:
+        Pc = api.Precond.build(X, kern, w["rank"], power_iters=w["power_iters"], seed=inputs.SEED_SKETCH,
+                               precision=args.sketch_precision)
+        handles = {"f32": Pc}
+
+        def timed_estimate(prec):
+            if prec == "fp64" and "f64" not in handles:
+                A_, D_, _ = Pc.export()
+                handles["f64"] = api.Precond.import_(A_, D_, "fp64")
+                del A_, D_
+            Ph = handles["f64" if prec == "fp64" else "f32"]
+            torch.cuda.synchronize()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            r_ = api.logdet_estimate(X, kern, precond=Ph, **dict(opts, precision=prec))
+            b_.record(stream)
+            torch.cuda.synchronize()
+            return a_.elapsed_time(b_), r_
+
+        ms_ref, r_ref = timed_estimate(args.precision)
+        estimate_compare = {"reference_precision": args.precision, "ms": ms_ref, "logdet": r_ref["logdet"],
+                            "std_err": r_ref["std_err"], "max_resid": r_ref["max_resid"][:w["order"]],
+                            "note": "same preconditioner (built once, sketch %s) and probes; ms excludes the "
+                                    "preconditioner build" % args.sketch_precision}
+        for prec in precs:
+            ms_p, r_p = timed_estimate(prec)
+            estimate_compare[prec] = {"ms": ms_p, "logdet": r_p["logdet"], "logdet_P": r_p["logdet_P"],
+                                      "rel_diff": abs(r_p["logdet"] - r_ref["logdet"]) / abs(r_p["logdet"]),
+                                      "max_resid": r_p["max_resid"][:w["order"]],
+                                      "speedup_of_%s" % args.precision: ms_p / ms_ref}
+        for h in handles.values():
+            h.free()
+
     kname = "matern52" if w["kind"] == inputs.MATERN52 else "rbf"
     peak = pair_peak_gps(kname, d)
     tc_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops") \
@@ -391,12 +449,8 @@ def run_ours(args, rank, world, local_rank, pool):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16x3", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "d": d, "kernel": kname, "lengthscale": w["lengthscale"],
-                   "variance": w["variance"], "noise": w["noise"], "order": w["order"], "rank": w["rank"],
-                   "power_iters": w["power_iters"], "probes": w["probes"], "lanczos_steps": args.t,
-                   "kz_precision": args.precision, "sketch_precision": args.sketch_precision,
-                   "residual_check": True, "parallelism": "independent estimate per GPU",
-                   "l2": "flushed between steps (256 MiB write, outside step events)"},
+        "config": dict(config_of(args, w), kz_precision=args.precision, sketch_precision=args.sketch_precision,
+                       parallelism="independent estimate per GPU"),
         "probe_matvecs_per_s": world * args.steps * (w["probes"] * args.t + w["probes"] * w["order"])
                                / (total_ms_max / 1e3),
         "sketch_matvecs_per_s": world * args.steps * (w["power_iters"] + 2) * w["rank"] / (total_ms_max / 1e3),
@@ -413,6 +467,7 @@ def run_ours(args, rank, world, local_rank, pool):
         "clocks": clk,
         "gpu_launches": int(launches),
         "e2e": e2e,
+        "estimate_precision_compare": estimate_compare,
     }
     if pool is not None:
         sec, sample = pool.estimate_seconds(args.t)
@@ -448,20 +503,23 @@ def run_ours(args, rank, world, local_rank, pool):
 
 
 def run_reference(args, pool):
+    """The oracle timed on the host cores: per step, the same row sample (ROWS_PER_CORE
+    rows per core of every product width) as our arm's cpu_baseline leg, extrapolated
+    to one estimate; the warm-up steps are sampled and discarded."""
     w = workload(args)
     cores = pool.cores
     vals = []
     sample = ""
     for k in range(args.warmup + args.steps):
-        sec, sample = pool.estimate_seconds(args.t, rows_per_core=1)
+        sec, sample = pool.estimate_seconds(args.t, rows_per_core=ROWS_PER_CORE)
         if k >= args.warmup:
             vals.append(1.0 / sec)
     value = statistics.mean(vals)
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "n": w["n"], "d": w["d"], "kernel": "matern52",
-                       "rank": w["rank"], "probes": w["probes"], "lanczos_steps": args.t},
+            "config": dict(config_of(args, w), kz_precision="fp64 (oracle)", sketch_precision="fp64 (oracle)",
+                           parallelism="host cores (process pool)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
