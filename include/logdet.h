@@ -184,7 +184,12 @@ int ld_kz_static(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
 
 /* Same pass computing both W = K V and W_dl = (dK/dl) V (for the gradient,
  * Section 3's CG-based gradient; derivative forms above).  noise is NOT added
- * to either.  FP64 and FP32 only. */
+ * to either.  LD_FP64 / LD_FP32: SIMT.  Tensor-core precisions (d <= 8): one
+ * tcgen05 pass evaluates k and dk/dl per pair with a shared exponential and
+ * accumulates both products in tensor memory, 64 columns per launch, in the
+ * precision's rounding of K, dK/dl and V (hi/lo fp16 for LD_F16X3_TC); the call
+ * allocates its scratch, synchronises the stream and returns
+ * LD_ERR_DEVICE_TIMEOUT if a device-side wait gave up. */
 int ld_kz_dl(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
              const void *V_dev, void *W_dev, void *Wdl_dev, int32_t c,
              int32_t precision, void *stream);
@@ -296,8 +301,9 @@ int ld_combine(const double *brackets_host, int32_t num_probes, double logdet_P,
  *   d/dtheta = (1/s) sum_i sum_j (-c_j) y_ij^T (dM/dtheta) y_ij,
  *   y_ij = L^-T x_ij,  x_ij = (B + sigma_j I)^-1 z_i,
  * for theta = (lengthscale, variance, noise) into grad_host[3], plus the
- * estimate itself in *out.  dM/dl = dK/dl, dM/dv = K/v, dM/dnu = I.
- * FP64 and FP32 precision only (the derivative pass is SIMT). */
+ * estimate itself in *out.  dM/dl = dK/dl, dM/dv = K/v, dM/dnu = I.  Every
+ * precision: the derivative pass (K y and dK/dl y for all s m columns) runs as
+ * ld_kz_dl does in that precision, the dots y^T (.) y in fp64. */
 int logdet_grad(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
                 const ld_precond *P, const ld_options *opt,
                 const int8_t *probes_dev, void *ws, size_t ws_bytes,
@@ -323,7 +329,8 @@ int ld_profile_end(double *kz_ms, int64_t *kz_launches, double *kz_pairs, double
 /* The same totals of the last closed window for one kernel: 0 the general
  * tensor-core product, 1 the symmetric tensor-core product, 2 the SIMT product,
  * 3 the stored dense product (CUDA-core GEMM or tensor cores), 4 the one-pass wide (256 < c <= 512) tensor-core
- * product.  LD_ERR_INVALID for another id. */
+ * product, 5 the tensor-core derivative pass of the gradient (K V and dK/dl V).  LD_ERR_INVALID for another
+ * id. */
 int ld_profile_kernel(int32_t kernel, double *ms, int64_t *launches, double *pairs, double *mma_flops);
 
 /* --------------------------------------------------------------- surrogate

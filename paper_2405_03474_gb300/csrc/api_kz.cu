@@ -67,11 +67,11 @@ int ld_kz_dl(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, const vo
     clear_error();
     LD_TRY(check_kz_args(X_dev, n, d, kern, V_dev, W_dev, c, precision));
     LD_REQUIRE(Wdl_dev && Wdl_dev != V_dev && Wdl_dev != W_dev, "ld_kz_dl: bad Wdl");
-    LD_REQUIRE(precision == LD_FP64 || precision == LD_FP32, "ld_kz_dl: FP64 or FP32 only");
     cudaStream_t st = (cudaStream_t)stream;
     Arena a;
     size_t elt = precision == LD_FP64 ? sizeof(double) : sizeof(float);
-    LD_TRY(arena_open(a, nullptr, 0, (size_t)n * d * elt + 256));
+    const size_t tc_ws = is_tc_precision(precision) ? kz_dl_tc_workspace(n, d, precision) : 0;
+    LD_TRY(arena_open(a, nullptr, 0, (size_t)n * d * elt + 256 + tc_ws));
     int code = [&]() -> int {
         if (precision == LD_FP64) {
             double *Xs = a.take<double>((size_t)n * d);
@@ -81,6 +81,9 @@ int ld_kz_dl(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, const vo
         }
         float *Xs = a.take<float>((size_t)n * d);
         LD_TRY(prep_points<float>(X_dev, n, d, point_scale(kern), Xs, st));
+        if (is_tc_precision(precision))
+            return kz_dl_tc(Xs, n, d, kern.kind, kern.lengthscale, kern.variance, (const float *)V_dev,
+                            (float *)W_dev, (float *)Wdl_dev, c, precision, a, st);
         return kz_dl_simt<float>(Xs, n, d, kern.kind, kern.lengthscale, kern.variance,
                                  (const float *)V_dev, (float *)W_dev, (float *)Wdl_dev, c, st);
     }();

@@ -399,6 +399,9 @@ size_t run_bytes(int64_t n, int d, const ld_precond *P, int s, int m, int max_it
     size_t tail = orth_probe_tail_bytes(n, s);
     const int cw = extra ? std::max(s, s * m) : s;
     if (!dense) tail = std::max(tail, kz_any_workspace<T>(n, d, cw, precision));
+    // the gradient's derivative pass on the tensor cores
+    if (extra && std::is_same<T, float>::value && is_tc_precision(precision))
+        tail = std::max(tail, kz_dl_tc_workspace(n, d, precision));
     else if (std::is_same<T, float>::value && is_tc_precision(precision))
         tail = std::max(tail, dense_tc_workspace(n, cw, precision));
     meas.take<char>(tail);
@@ -564,8 +567,17 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
                 } else {
                     LD_CHECK_CUDA(cudaMemcpyAsync(b.Y, b.Xall, nsm * sizeof(T), cudaMemcpyDeviceToDevice, st));
                 }
-                LD_TRY(kz_dl_simt<T>(b.Xs, n, d, kern.kind, kern.lengthscale, kern.variance, b.Y, b.W1,
-                                     b.W2, sm, st));
+                bool dl_done = false;
+                if constexpr (std::is_same<T, float>::value) {
+                    if (is_tc_precision(o.precision)) {
+                        LD_TRY(kz_dl_tc(b.Xs, n, d, kern.kind, kern.lengthscale, kern.variance, b.Y, b.W1, b.W2,
+                                        sm, o.precision, a, st));
+                        dl_done = true;
+                    }
+                }
+                if (!dl_done)
+                    LD_TRY(kz_dl_simt<T>(b.Xs, n, d, kern.kind, kern.lengthscale, kern.variance, b.Y, b.W1,
+                                         b.W2, sm, st));
                 LD_TRY(coldot<T>(n, sm, b.Y, b.W2, b.gdots, b.part, st));
                 LD_TRY(coldot<T>(n, sm, b.Y, b.W1, b.gdots + sm, b.part, st));
                 LD_TRY(coldot<T>(n, sm, b.Y, b.Y, b.gdots + 2 * sm, b.part, st));
@@ -618,8 +630,6 @@ int validate(const double *X, int64_t n, int d, const ld_kernel &k, const ld_pre
         LD_REQUIRE((P->precision == LD_FP64) == (o->precision == LD_FP64),
                    "preconditioner and estimate must both be FP64 or both be non-FP64");
     }
-    if (grad) LD_REQUIRE(o->precision == LD_FP64 || o->precision == LD_FP32,
-                         "logdet_grad supports LD_FP64 and LD_FP32");
     return LD_OK;
 }
 

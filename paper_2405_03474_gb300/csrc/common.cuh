@@ -70,7 +70,8 @@ inline int check_launch(const char *what, int launches = 1) {
 // Optional timing of the kernel-product launches (CUDA events on the launch
 // stream), enabled between ld_profile_begin and ld_profile_end.
 // kernel ids of the profile totals (ld_profile_kernel)
-enum { PROF_KZ_TC = 0, PROF_KZ_SYM = 1, PROF_KZ_SIMT = 2, PROF_DENSE = 3, PROF_KZ_WIDE = 4, PROF_KERNELS = 5 };
+enum { PROF_KZ_TC = 0, PROF_KZ_SYM = 1, PROF_KZ_SIMT = 2, PROF_DENSE = 3, PROF_KZ_WIDE = 4, PROF_KZ_DL = 5,
+       PROF_KERNELS = 6 };
 int prof_begin_launch(cudaStream_t st, int kernel, double pairs, double mma_flops);  // -1 when off
 void prof_end_launch(cudaStream_t st, int slot);
 
@@ -133,6 +134,12 @@ int kz_simt(const T *Xs, int64_t n, int d, int kind, double variance, double noi
 template <typename T>
 int kz_dl_simt(const T *Xs, int64_t n, int d, int kind, double lengthscale, double variance,
                const T *V, T *W, T *Wdl, int c, cudaStream_t st);
+
+// W = K V, Wdl = (dK/dl) V on the tensor cores (no noise), any number of columns
+// (kz_dl_tc.cu); Xs pre-scaled like every product
+size_t kz_dl_tc_workspace(int64_t n, int d, int precision);
+int kz_dl_tc(const float *Xs, int64_t n, int d, int kind, double lengthscale, double variance, const float *V,
+             float *W, float *Wdl, int c, int precision, Arena &ws, cudaStream_t st);
 
 // stored dense M = K + noise I (row-major n x n) and W = M V (dense_path.cu)
 template <typename T>

@@ -173,3 +173,20 @@ def test_kz_symmetric_tensor_core_matches_oracle(prec, kind, n, d, c):
     W = host(api.ld_kz(cuda(X), cuda(V, torch.float32), k, prec))
     M = kernels.kernel_matrix(X, kind, 0.2, 0.9, 3e-2)
     assert_elementwise(W, M @ V, product_scale(M, V), TC_TOL[prec])
+
+
+# The gradient's derivative pass on the tensor cores: K V and dK/dl V from one sweep,
+# 64 columns per launch (100 columns: two launches), ragged n, d up to 6.
+@pytest.mark.parametrize("prec", ["f16x3_tc", "f16_tc", "bf16_tc"])
+@pytest.mark.parametrize("kind", [api.RBF, api.MATERN52])
+@pytest.mark.parametrize("n,d,c", [(1000, 2, 16), (777, 4, 48), (300, 3, 5), (2000, 4, 100), (129, 1, 64),
+                                   (700, 6, 7)])
+def test_kz_dl_tensor_core_matches_oracle(prec, kind, n, d, c):
+    X = inputs.points(n, d, "uniform", seed=13)
+    V = inputs.gaussian(n, c, seed=14)
+    k = api.Kernel(kind, 0.2, 1.3, 0.0)
+    W, Wdl = api.ld_kz_dl(cuda(X), cuda(V, torch.float32), k, prec)
+    K = kernels.kernel_matrix(X, kind, 0.2, 1.3, 0.0)
+    dK = kernels.dkernel_dl_matrix(X, kind, 0.2, 1.3)
+    assert_elementwise(host(W), K @ V, product_scale(K, V), TC_TOL[prec], "K V")
+    assert_elementwise(host(Wdl), dK @ V, product_scale(dK, V), TC_TOL[prec], "dK/dl V")

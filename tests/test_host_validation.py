@@ -84,10 +84,12 @@ def test_preconditioner_import_checks(lib):
 
 def test_profile_kernel_id_check(lib):
     ms, nl, pairs, flops = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
-    assert lib.ld_profile_kernel(5, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(pairs),
-                                 ctypes.byref(flops)) == _lib.LD_ERR_INVALID
-    assert lib.ld_profile_kernel(1, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(pairs),
-                                 ctypes.byref(flops)) == _lib.LD_OK
+    for bad in (-1, 6):
+        assert lib.ld_profile_kernel(bad, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(pairs),
+                                     ctypes.byref(flops)) == _lib.LD_ERR_INVALID
+    for good in (1, 5):  # the symmetric product, the tensor-core derivative pass
+        assert lib.ld_profile_kernel(good, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(pairs),
+                                     ctypes.byref(flops)) == _lib.LD_OK
 
 
 def test_dense_product_argument_checks(lib):
