@@ -280,7 +280,10 @@ void precond_free(ld_precond *P);
  * Returns LD_ERR_INVALID for a NaN or Inf coordinate in X (checked on the
  * device first), LD_ERR_NOT_CONVERGED (with *out filled) when rel_tol was not
  * met, and LD_ERR_NOT_SPD (with *out filled) when the estimate is not finite
- * (a matrix that is not SPD). */
+ * or a CG column met p^T (B + sigma_min) p <= 0 (a matrix that is not SPD; in the
+ * reduced precisions this happens when the rounding of K, about 2^-8 (bf16),
+ * 2^-11 (fp16), 2^-22 (hi/lo fp16) of each entry times the largest row sum of K,
+ * reaches the noise on the diagonal). */
 size_t logdet_workspace_size(int64_t n, int32_t d, const ld_precond *P,
                              const ld_options *opt);
 int logdet_estimate(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,

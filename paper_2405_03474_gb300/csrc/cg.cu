@@ -29,6 +29,7 @@ struct ColState {
     double rho, znorm2, alpha, alpha_prev, beta, beta_prev;
     double zeta[5], zeta_prev[5], zeta_next[5], alpha_s[5], beta_s[5];
     int active, upd, t, live[5];
+    int broke;  // p^T (B + sigma_min) p <= 0 was met: the operator is not positive definite
 };
 
 struct Shifts {
@@ -55,6 +56,7 @@ __global__ void cg_init_kernel(ColState *cs, const double *rr, int s, int m) {
         st.live[j] = j < m ? 1 : 0;
     }
     st.active = rr[c] > 0.0 ? 1 : 0;
+    st.broke = 0;
     st.upd = 0;
     st.t = 0;
     cs[c] = st;
@@ -73,7 +75,9 @@ __global__ void cg_alpha_kernel(ColState *cs, const double *pBp, int s, Shifts s
         return;
     }
     double a = st.rho / pBp[c];
-    if (!(a > 0.0) || !isfinite(a) || st.t >= max_iters) {  // breakdown: stop this column
+    if (!(a > 0.0) || !isfinite(a) || st.t >= max_iters) {  // breakdown or cap: stop this column
+        // a column whose residual is already at rounding level may meet p^T B p <= 0 harmlessly
+        if (st.t < max_iters && st.rho > 1e-28 * st.znorm2) st.broke = 1;
         st.active = 0;
         st.alpha = 0.0;
         for (int j = 0; j < sh.m; ++j) st.alpha_s[j] = 0.0;
@@ -437,6 +441,7 @@ struct RunOut {
     std::vector<double> brackets, slq;
     int iters = 0;
     bool converged = true;
+    int broke = 0;  // columns whose CG met p^T (B + sigma_min) p <= 0
     double final_rel = 0.0;
     double max_resid[5] = {0, 0, 0, 0, 0};
     double grad[3] = {0, 0, 0};
@@ -539,6 +544,7 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
                 out.final_rel = std::max(out.final_rel, rel);
                 if (o.fixed_iters == 0 && !(cs[c].rho < tol2 * cs[c].znorm2) && cs[c].rho > 0)
                     out.converged = false;
+                out.broke += cs[c].broke;
             }
             if (!vectors) continue;
             const int sm = s * m;
@@ -707,6 +713,11 @@ int logdet_estimate(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, c
                   "finite SPD matrix", out->logdet_P, out->trace_est);
         return LD_ERR_NOT_SPD;
     }
+    if (r.broke) {
+        set_error("CG breakdown in %d column(s): p^T (B + sigma) p <= 0, the operator in this precision is not "
+                  "positive definite (the rounding of K exceeds the noise; use a wider precision)", r.broke);
+        return LD_ERR_NOT_SPD;
+    }
     if (!r.converged) {
         set_error("CG did not reach rel_tol %.3g in %d iterations (final %.3g)", opt->rel_tol,
                   opt->max_iters, r.final_rel);
@@ -741,6 +752,11 @@ int logdet_grad(const double *X_dev, int64_t n, int32_t d, ld_kernel kern, const
     if (!isfinite(out->logdet) || !isfinite(r.grad[0]) || !isfinite(r.grad[1]) || !isfinite(r.grad[2])) {
         set_error("non-finite estimate or gradient: the points or kernel parameters do not give a finite SPD "
                   "matrix");
+        return LD_ERR_NOT_SPD;
+    }
+    if (r.broke) {
+        set_error("CG breakdown in %d column(s): p^T (B + sigma) p <= 0, the operator in this precision is not "
+                  "positive definite", r.broke);
         return LD_ERR_NOT_SPD;
     }
     if (!r.converged) {

@@ -419,7 +419,11 @@ int launch_wide_d(const WideParams &p, const WideLayout &L, int nblocks, cudaStr
     }
 }
 
-int wide_N(int c) { return ((c + 31) / 32) * 32; }  // a multiple of 32: 4 epilogue spans of whole 8-column loads
+// Always the full 512 columns (the second 256-column half at full width; columns past c are
+// zero in the image and discarded).  Narrower second halves (N - 256 < 256) produced, in about
+// one call in seven with RBF at 300 columns, one wrong 8-row group of a tile when the MMA and
+// evaluation sides ran at nearly the same rate; at full width no repeat differed.
+int wide_N(int c) { (void)c; return W_MAXN; }
 
 }  // namespace
 

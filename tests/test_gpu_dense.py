@@ -143,3 +143,45 @@ def test_rbf_n65536_stored_dense_at_full_size():
         print("dense estimate %s: log det %.6f (trace %.6f), %.2f s"
               % (prec, res[prec]["logdet"], res[prec]["trace_est"], time.perf_counter() - t0))
     assert res["f16x3_tc"]["logdet"] == pytest.approx(res["fp32"]["logdet"], rel=1e-4)
+
+
+def test_rbf_n65536_orders_and_precisions_against_fp64():
+    # The stored-dense workload as stated: r_1, r_3 and r_5 with a rank-256 preconditioner
+    # and 64 probes, M stored (fp64 for the reference, fp32 for the others), the estimate
+    # in FP32 (CUDA-core GEMM), hi/lo fp16 and bf16 on the tensor cores, each against the
+    # FP64 estimate on the same probes, preconditioner and t (the FP64 path matches the
+    # oracle to 1e-10 at every size it can check).
+    import time
+    from paper_2405_03474_gb300.inputs import SEED_POINTS, SEED_PROBES, WORKLOADS
+    w = WORKLOADS["rbf_n65536_d3"]
+    n, d, s, t = w["n"], w["d"], w["probes"], 40
+    X = inputs.points(n, d, w["dist"], seed=SEED_POINTS)
+    k = api.Kernel(w["kind"], w["lengthscale"], w["variance"], w["noise"])
+    Xt = cuda(X)
+    P32 = api.Precond.build(Xt, k, w["rank"], power_iters=w["power_iters"], seed=2, precision="f16_tc")
+    A, D, _ = P32.export()
+    P64 = api.Precond.import_(A, D, "fp64")
+    del A, D
+    Z = cuda(inputs.rademacher(n, s, seed=SEED_PROBES))
+    from paper_2405_03474_gb300 import _lib
+    for order in (1, 3, 5):
+        res = {}
+        for prec in ("fp64", "fp32", "f16x3_tc", "bf16_tc"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                res[prec] = api.logdet_estimate(Xt, k, precond=P64 if prec == "fp64" else P32, probes=Z,
+                                                order=order, num_probes=s, precision=prec, fixed_iters=t,
+                                                max_iters=t, dense=True)
+            except _lib.LogdetError as e:
+                # bf16 kernel values (8 bits) perturb M by ~2^-9 of its row sums, far above the
+                # noise 1e-3: the operator is not positive definite and CG says so
+                assert prec == "bf16_tc" and e.status == _lib.LD_ERR_NOT_SPD, (prec, str(e))
+                print("rbf_n65536 r_%d %s: %s" % (order, prec, e))
+                continue
+            sec = time.perf_counter() - t0
+            ref = res["fp64"]["logdet"]
+            print("rbf_n65536 r_%d %s: log det %.6f, %.2f s, rel err vs FP64 %.2e"
+                  % (order, prec, res[prec]["logdet"], sec, abs(res[prec]["logdet"] / ref - 1)))
+        for prec in ("fp32", "f16x3_tc"):
+            assert res[prec]["logdet"] == pytest.approx(res["fp64"]["logdet"], rel=1e-4), (order, prec)

@@ -190,3 +190,34 @@ def test_kz_dl_tensor_core_matches_oracle(prec, kind, n, d, c):
     dK = kernels.dkernel_dl_matrix(X, kind, 0.2, 1.3)
     assert_elementwise(host(W), K @ V, product_scale(K, V), TC_TOL[prec], "K V")
     assert_elementwise(host(Wdl), dK @ V, product_scale(dK, V), TC_TOL[prec], "dK/dl V")
+
+
+# Repetition: the general, wide and derivative products reduce in a fixed order, so the same
+# call must give the same bits every time; a race between the evaluation and MMA sides shows
+# up as an occasional wrong tile.  (The symmetric product adds transposed blocks in arrival
+# order, so it is repeated against the oracle instead.)
+@pytest.mark.parametrize("prec,c", [("bf16_tc", 300), ("f16_tc", 300), ("f16_tc", 264), ("f16x3_tc", 100)])
+def test_deterministic_products_repeat_bit_for_bit(prec, c):
+    n, d = 5000, 4
+    X = cuda(inputs.points(n, d, "uniform", seed=21))
+    V = cuda(inputs.gaussian(n, c, seed=23), torch.float32)
+    k = api.Kernel(api.RBF, 0.15, 1.2, 1e-2)
+    first = api.ld_kz(X, V, k, prec).clone()
+    for rep in range(30):
+        assert torch.equal(api.ld_kz(X, V, k, prec), first), (prec, c, rep)
+    W1, G1 = api.ld_kz_dl(X, V[:, :48].contiguous(), k, "f16x3_tc")
+    for rep in range(10):
+        W2, G2 = api.ld_kz_dl(X, V[:, :48].contiguous(), k, "f16x3_tc")
+        assert torch.equal(W1, W2) and torch.equal(G1, G2), rep
+
+
+def test_symmetric_product_repeats_against_oracle():
+    n, d, c = 5000, 4, 16
+    Xh = inputs.points(n, d, "uniform", seed=24)
+    Vh = inputs.gaussian(n, c, seed=25)
+    k = api.Kernel(api.RBF, 0.15, 1.2, 1e-2)
+    M = kernels.kernel_matrix(Xh, api.RBF, 0.15, 1.2, 1e-2)
+    X, V = cuda(Xh), cuda(Vh, torch.float32)
+    ref, scale = M @ Vh, product_scale(M, Vh)
+    for rep in range(15):
+        assert_elementwise(host(api.ld_kz(X, V, k, "f16x3_tc")), ref, scale, TC_TOL["f16x3_tc"], "repeat %d" % rep)
