@@ -43,11 +43,11 @@ ROWS_PER_CORE = 4
 
 
 # DRAM traffic of one launch of the dominant kernel (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum, one pass, n = 2^20, 16 columns, hi/lo fp16: 1.02 GB read +
-# 0.60 GB written), valid only for the kernel sources it was taken on (first 16 hex
+# dram__bytes_write.sum, one pass, n = 2^20, 16 columns, hi/lo fp16: 1.04 GB read +
+# 0.74 GB written), valid only for the kernel sources it was taken on (first 16 hex
 # digits of their sha256); reported as null once those sources change.
-KZ_SYM_TRAFFIC = {"bytes": 1.02e9 + 0.59641e9, "sources": {"paper_2405_03474_gb300/csrc/kz_sym.cu": "2ec2b0d7ba589475",
-                                                          "paper_2405_03474_gb300/csrc/tc_common.cuh": "efe385d1449bd0a8"}}
+KZ_SYM_TRAFFIC = {"bytes": 1.04e9 + 0.74192e9, "sources": {"paper_2405_03474_gb300/csrc/kz_sym.cu": "b7baadfa39d6bc2d",
+                                                          "paper_2405_03474_gb300/csrc/tc_common.cuh": "9ab49c92642e95a3"}}
 
 
 def measured_traffic(record):
@@ -110,6 +110,14 @@ def parse():
                     help="comma-separated precisions whose estimate is run once after the timed region with the "
                          "same preconditioner and probes ('' to skip; fp64 imports the preconditioner's factors "
                          "into an FP64 handle)")
+    ap.add_argument("--no-grad-side", action="store_true",
+                    help="skip the gradient side line (logdet_grad on the 2^17-point gradient workload)")
+    ap.add_argument("--dense-only", type=int, default=0, metavar="N",
+                    help="profiling aid: the stored-M tensor-core product (hi/lo fp16, 64 columns) on N points of "
+                         "the stored-dense workload (2 warm-up + 1 launch)")
+    ap.add_argument("--cg-only", action="store_true",
+                    help="profiling aid: one estimate at --n with a rank-64 preconditioner and 2 CG steps (the CG "
+                         "vector updates and preconditioner applies at full vector size)")
     ap.add_argument("--kz-only", type=int, default=0, metavar="C",
                     help="profiling aid: run only the kernel product on C columns (2 warm-up + 1 launch)")
     return ap.parse_args()
@@ -413,6 +421,8 @@ def run_ours(args, rank, world, local_rank, pool):
         for h in handles.values():
             h.free()
 
+    grad_side = None if args.no_grad_side else gradient_side(stream)
+
     kname = "matern52" if w["kind"] == inputs.MATERN52 else "rbf"
     peak = pair_peak_gps(kname, d)
     tc_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops") \
@@ -468,6 +478,7 @@ def run_ours(args, rank, world, local_rank, pool):
         "gpu_launches": int(launches),
         "e2e": e2e,
         "estimate_precision_compare": estimate_compare,
+        "gradient_side": grad_side,
     }
     if pool is not None:
         sec, sample = pool.estimate_seconds(args.t)
@@ -500,6 +511,44 @@ def run_ours(args, rank, world, local_rank, pool):
                 cmp[prec]["speedup_vs_fp32"] = cmp["fp32"]["ms"] / cmp[prec]["ms"]
             line["kz_precision_compare"] = {"columns": w["probes"], "n": n, **cmp}
     return line
+
+
+def gradient_side(stream):
+    """The hand-written adjoint on the gradient workload's points (n = 2^17 uniform in
+    [0,1]^2, RBF, 16 probes, rank-128 preconditioner), once in hi/lo fp16 on the tensor
+    cores and once in FP32 SIMT with the same preconditioner and probes, at the
+    hyperparameters (0.2, 1, 0.1) where the hi/lo fp16 operator is well inside positive
+    definiteness; time by CUDA events (the preconditioner build excluded) and the
+    relative difference of the two gradients."""
+    import numpy as np
+    import torch
+    from paper_2405_03474_gb300 import api, inputs
+    w = inputs.WORKLOADS["rbf_grad_n131072_d2"]
+    th = (0.2, 1.0, 0.1)
+    n, d, s_ = w["n"], w["d"], 16
+    X = torch.as_tensor(inputs.points(n, d, w["dist"], seed=inputs.SEED_POINTS)).cuda()
+    kern = api.Kernel(w["kind"], *th)
+    P = api.Precond.build(X, kern, w["rank"], power_iters=w["power_iters"], seed=inputs.SEED_SKETCH,
+                          precision="f16_tc")
+    Z = torch.as_tensor(inputs.rademacher(n, s_, seed=inputs.SEED_PROBES)).cuda()
+    out = {"workload": "rbf_grad_n131072_d2", "theta": th, "probes": s_, "rank": w["rank"], "rel_tol": 1e-6}
+    for prec in ("f16x3_tc", "fp32"):
+        api.logdet_grad(X, kern, precond=P, probes=Z, order=3, num_probes=s_, precision=prec, rel_tol=1e-6,
+                        max_iters=3000)  # warm
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = api.logdet_grad(X, kern, precond=P, probes=Z, order=3, num_probes=s_, precision=prec, rel_tol=1e-6,
+                            max_iters=3000)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[prec] = {"ms": a.elapsed_time(b), "grad": [float(g) for g in r["grad"]], "iters": r["iters"],
+                     "logdet": r["logdet"]}
+    g16, g32 = np.array(out["f16x3_tc"]["grad"]), np.array(out["fp32"]["grad"])
+    out["rel_diff"] = [float(v) for v in np.abs(g16 - g32) / np.abs(g32)]
+    out["speedup_of_f16x3_tc"] = out["fp32"]["ms"] / out["f16x3_tc"]["ms"]
+    P.free()
+    return out
 
 
 def run_reference(args, pool):
@@ -540,10 +589,44 @@ def run_kz_only(args):
     return 0
 
 
+def run_dense_only(args):
+    """Small case for ncu: the stored-M tensor-core product, N points of the stored-dense workload."""
+    import torch
+    from paper_2405_03474_gb300 import api, inputs
+    w = inputs.WORKLOADS["rbf_n65536_d3"]
+    n = args.dense_only
+    X = torch.as_tensor(inputs.points(n, w["d"], w["dist"], seed=inputs.SEED_POINTS)).cuda()
+    M = api.ld_dense_materialize(X, api.Kernel(w["kind"], w["lengthscale"], w["variance"], w["noise"]), "fp32")
+    V = torch.as_tensor(inputs.gaussian(n, 64, seed=2), dtype=torch.float32).cuda()
+    for _ in range(3):
+        W = api.ld_dense_kz(M, V, "f16x3_tc")
+    torch.cuda.synchronize()
+    print(json.dumps({"dense_only": True, "n": n, "c": 64, "checksum": float(W.double().abs().sum())}))
+    return 0
+
+
+def run_cg_only(args):
+    """Small case for ncu: one estimate of the workload with a rank-64 preconditioner and t = 2."""
+    import torch
+    from paper_2405_03474_gb300 import api, inputs
+    w = workload(args)
+    X = torch.as_tensor(inputs.points(w["n"], w["d"], w["dist"], seed=inputs.SEED_POINTS)).cuda()
+    kern = api.Kernel(w["kind"], w["lengthscale"], w["variance"], w["noise"])
+    P = api.Precond.build(X, kern, 64, power_iters=1, seed=inputs.SEED_SKETCH, precision=args.sketch_precision)
+    r = api.logdet_estimate(X, kern, precond=P, order=w["order"], num_probes=w["probes"], fixed_iters=2,
+                            max_iters=2, precision=args.precision, residual_check=True)
+    print(json.dumps({"cg_only": True, "n": w["n"], "logdet": r["logdet"]}))
+    return 0
+
+
 def main():
     args = parse()
     if args.kz_only:
         return run_kz_only(args)
+    if args.dense_only:
+        return run_dense_only(args)
+    if args.cg_only:
+        return run_cg_only(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -139,38 +139,145 @@ __global__ void cg_beta_kernel(ColState *cs, const double *rr_new, int s, Shifts
     if (threadIdx.x == 0) atomicAdd(n_active, cnt);
 }
 
-// r -= alpha Bp;  x_j += alpha^sigma_j p_j   (columns with upd only)
+// The CG vector updates are flat passes over n x s blocks (HBM-bound).  Each block
+// stages the s columns' coefficients in shared memory once (a frozen shift j or a
+// column without an update gets a zero flag), then every thread updates G = 4
+// consecutive columns of one row with 16-byte accesses when s % 4 == 0 (else G = 1).
+constexpr int CG_UPD_THREADS = 256;
+
 template <typename T>
-__global__ void cg_update_r_kernel(int64_t n, int s, int m, const ColState *cs, const T *Bp, T *r,
-                                   const T *ps, T *xs) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n * s) return;
-    int c = (int)(t % s);
-    const ColState &st = cs[c];
-    if (!st.upd) return;
-    r[t] -= (T)st.alpha * Bp[t];
-    if (xs) {
-        const size_t ns = (size_t)n * s;
-        for (int j = 0; j < m; ++j)
-            if (st.live[j]) xs[j * ns + t] += (T)st.alpha_s[j] * ps[j * ns + t];
+struct CgCoef {
+    T alpha[256], beta[256], zeta[5][256], as[5][256], bs[5][256];
+    unsigned char upd[256], live[5][256];
+};
+
+template <typename T>
+__device__ void cg_load_coef(const ColState *cs, int s, int m, CgCoef<T> &k) {
+    for (int c = threadIdx.x; c < s; c += blockDim.x) {
+        const ColState &st = cs[c];
+        k.upd[c] = (unsigned char)st.upd;
+        k.alpha[c] = (T)st.alpha;
+        k.beta[c] = (T)st.beta;
+        for (int j = 0; j < m; ++j) {
+            k.live[j][c] = (unsigned char)st.live[j];
+            k.as[j][c] = (T)st.alpha_s[j];
+            k.bs[j][c] = (T)st.beta_s[j];
+            k.zeta[j][c] = (T)st.zeta[j];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int G>
+struct Vec;
+template <typename T>
+struct Vec<T, 1> {
+    T v[1];
+    __device__ void load(const T *p) { v[0] = *p; }
+    __device__ void store(T *p) const { *p = v[0]; }
+};
+template <>
+struct Vec<float, 4> {
+    float v[4];
+    __device__ void load(const float *p) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    __device__ void store(float *p) const { *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]); }
+};
+template <>
+struct Vec<double, 4> {
+    double v[4];
+    __device__ void load(const double *p) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ void store(double *p) const {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    }
+};
+
+// r -= alpha Bp;  x_j += alpha^sigma_j p_j   (columns with upd only)
+template <typename T, int G>
+__global__ void __launch_bounds__(CG_UPD_THREADS) cg_update_r_kernel(int64_t n, int s, int m, const ColState *cs,
+                                                                      const T *Bp, T *r, const T *ps, T *xs) {
+    __shared__ CgCoef<T> k;
+    cg_load_coef<T>(cs, s, m, k);
+    const int sg = s / G;  // groups of G columns per row
+    const int64_t total = n * sg;
+    const size_t ns = (size_t)n * s;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = q / sg;
+        const int c0 = (int)(q - row * sg) * G;
+        const size_t e = (size_t)row * s + c0;
+        bool any = false;
+#pragma unroll
+        for (int g = 0; g < G; ++g) any |= k.upd[c0 + g] != 0;
+        if (!any) continue;
+        Vec<T, G> rv, bv;
+        rv.load(r + e);
+        bv.load(Bp + e);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (k.upd[c0 + g]) rv.v[g] -= k.alpha[c0 + g] * bv.v[g];
+        rv.store(r + e);
+        if (xs) {
+            for (int j = 0; j < m; ++j) {
+                Vec<T, G> xv, pv;
+                xv.load(xs + j * ns + e);
+                pv.load(ps + j * ns + e);
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (k.upd[c0 + g] && k.live[j][c0 + g]) xv.v[g] += k.as[j][c0 + g] * pv.v[g];
+                xv.store(xs + j * ns + e);
+            }
+        }
     }
 }
 
 // p = r + beta p;  p_j = zeta_j r + beta^sigma_j p_j
-template <typename T>
-__global__ void cg_update_p_kernel(int64_t n, int s, int m, ColState *cs, const T *r, T *p, T *ps) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n * s) return;
-    int c = (int)(t % s);
-    const ColState &st = cs[c];
-    if (!st.upd) return;
-    T rv = r[t];
-    p[t] = rv + (T)st.beta * p[t];
-    if (ps) {
-        const size_t ns = (size_t)n * s;
-        for (int j = 0; j < m; ++j)
-            if (st.live[j]) ps[j * ns + t] = (T)st.zeta[j] * rv + (T)st.beta_s[j] * ps[j * ns + t];
+template <typename T, int G>
+__global__ void __launch_bounds__(CG_UPD_THREADS) cg_update_p_kernel(int64_t n, int s, int m, const ColState *cs,
+                                                                      const T *r, T *p, T *ps) {
+    __shared__ CgCoef<T> k;
+    cg_load_coef<T>(cs, s, m, k);
+    const int sg = s / G;
+    const int64_t total = n * sg;
+    const size_t ns = (size_t)n * s;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = q / sg;
+        const int c0 = (int)(q - row * sg) * G;
+        const size_t e = (size_t)row * s + c0;
+        bool any = false;
+#pragma unroll
+        for (int g = 0; g < G; ++g) any |= k.upd[c0 + g] != 0;
+        if (!any) continue;
+        Vec<T, G> rv, pv;
+        rv.load(r + e);
+        pv.load(p + e);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (k.upd[c0 + g]) pv.v[g] = rv.v[g] + k.beta[c0 + g] * pv.v[g];
+        pv.store(p + e);
+        if (ps) {
+            for (int j = 0; j < m; ++j) {
+                Vec<T, G> qv;
+                qv.load(ps + j * ns + e);
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (k.upd[c0 + g] && k.live[j][c0 + g])
+                        qv.v[g] = k.zeta[j][c0 + g] * rv.v[g] + k.bs[j][c0 + g] * qv.v[g];
+                qv.store(ps + j * ns + e);
+            }
+        }
     }
+}
+
+// grid of the update kernels: a few waves of 256-thread blocks over the G-column groups
+inline unsigned cg_upd_grid(int64_t n, int s, int G) {
+    const int64_t groups = n * (s / G);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((groups + CG_UPD_THREADS - 1) / CG_UPD_THREADS, 152 * 16));
 }
 
 __global__ void cg_freeze_shifts_kernel(ColState *cs, int s, int m) {
@@ -510,12 +617,22 @@ int run_impl(const double *X, int64_t n, int d, const ld_kernel &kern, const ld_
                 LD_TRY(apply_B<T>(P, b, b.Xs, n, d, kern, b.p, b.Bp, b.y, b.w, s, smin, o.precision, a, st));
                 LD_TRY(coldot<T>(n, s, b.p, b.Bp, b.dots, b.part, st));
                 cg_alpha_kernel<<<nb(s, 128), 128, 0, st>>>(b.cs, b.dots, s, sh, b.hist_a, max_iters);
-                cg_update_r_kernel<T><<<nb(ns), 256, 0, st>>>(n, s, m, b.cs, b.Bp, b.r, b.ps, b.xs);
+                if (s % 4 == 0)
+                    cg_update_r_kernel<T, 4><<<cg_upd_grid(n, s, 4), CG_UPD_THREADS, 0, st>>>(n, s, m, b.cs, b.Bp, b.r,
+                                                                                             b.ps, b.xs);
+                else
+                    cg_update_r_kernel<T, 1><<<cg_upd_grid(n, s, 1), CG_UPD_THREADS, 0, st>>>(n, s, m, b.cs, b.Bp, b.r,
+                                                                                             b.ps, b.xs);
                 LD_TRY(coldot<T>(n, s, b.r, b.r, b.dots + s, b.part, st));
                 LD_CHECK_CUDA(cudaMemsetAsync(b.n_active, 0, sizeof(int), st));
                 cg_beta_kernel<<<nb(s, 128), 128, 0, st>>>(b.cs, b.dots + s, s, sh, b.hist_b, tol2,
                                                           o.fixed_iters, b.n_active);
-                cg_update_p_kernel<T><<<nb(ns), 256, 0, st>>>(n, s, m, b.cs, b.r, b.p, b.ps);
+                if (s % 4 == 0)
+                    cg_update_p_kernel<T, 4><<<cg_upd_grid(n, s, 4), CG_UPD_THREADS, 0, st>>>(n, s, m, b.cs, b.r, b.p,
+                                                                                             b.ps);
+                else
+                    cg_update_p_kernel<T, 1><<<cg_upd_grid(n, s, 1), CG_UPD_THREADS, 0, st>>>(n, s, m, b.cs, b.r, b.p,
+                                                                                             b.ps);
                 cg_freeze_shifts_kernel<<<nb(s, 128), 128, 0, st>>>(b.cs, s, m);
                 LD_TRY(check_launch("cg iteration", 5));
                 int n_active = 0;
