@@ -135,6 +135,11 @@ template <typename T>
 int kz_dl_simt(const T *Xs, int64_t n, int d, int kind, double lengthscale, double variance,
                const T *V, T *W, T *Wdl, int c, cudaStream_t st);
 
+// A spatially coherent order of the n points (Morton codes over the bounding box, stable
+// radix sort): perm[r] is the point at position r (point_order.cu); d <= 8, n < 2^31.
+size_t point_order_workspace(int64_t n, int d);
+int point_order(const float *Xs, int64_t n, int d, int *perm, Arena &ws, cudaStream_t st);
+
 // W = K V, Wdl = (dK/dl) V on the tensor cores (no noise), any number of columns
 // (kz_dl_tc.cu); Xs pre-scaled like every product
 size_t kz_dl_tc_workspace(int64_t n, int d, int precision);

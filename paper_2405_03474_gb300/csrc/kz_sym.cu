@@ -22,9 +22,18 @@
 // sums, held in registers (each eval thread owns a quarter of one row's columns),
 // as in the non-symmetric kernel.  The kernel is compiled for SN = 16 and SN = 48
 // columns (padded).  Every mbarrier wait is bounded.
+//
+// The tiles hold the points in Morton order (point_order.cu), so most tiles are compact
+// and most pairs of tiles are far apart.  With the hi/lo split, a block whose tiles'
+// boxes are so far apart that every kernel value is <= 2^-10 (of the variance) is rounded
+// to fp16 once and its K_lo products are skipped: one rounding of such values errs by at
+// most 2^-21, no more than the split does near 1.  Rows of W and V are reached through
+// the permutation.
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "tc_common.cuh"
@@ -44,14 +53,16 @@ constexpr int CORE_SBO = (BR / 8) * 128;    // 2048: byte step between 8-row gro
 constexpr int SN_MAX = 48;
 
 struct SymParams {
+    const float *tbox;   // per tile: d minima then d maxima of its coordinates (kernel units)
+    float thr2;          // squared distance (kernel units) beyond which k <= 2^-10: one fp16 rounding
+    int far_on;          // 1: blocks between tiles at least sqrt(thr2) apart skip the hi/lo split
     const float *Xp;     // per 128-point tile: d x 128 floats, far-padded, log2 e folded in
     const uint8_t *img;  // per 128-point tile: nprod x (SN x 128) halves, canonical K-major
-    const float *V;      // n x c
     const float *colinv; // 1 / column scale (SN)
-    float *W;            // zeroed; every contribution is added
+    float *W;            // n x c in tile order (row r is point perm[r]); zeroed, every contribution added
     int64_t n;
     int d, c, NB, ncols_tmem, vec_ok;
-    float variance, noise;
+    float variance;
     int *err;
 };
 
@@ -121,6 +132,9 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
     uint64_t *tempty = tfull + 2;                         // [2] D' drained
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
     int *s_err = reinterpret_cast<int *>(tmem_slot + 1);
+    // per load stage: 1 if the block in it is far (single fp16, no K_lo products); written
+    // by the producer before the stage's copies are issued, read after its full barrier
+    volatile int *s_far = reinterpret_cast<volatile int *>(s_err + 1);
     uint8_t *abase = smem + L.a_off;
     uint8_t *lbase = smem + L.l_off;
     uint8_t *vimg = smem + L.vi_off;
@@ -172,26 +186,62 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
     const uint32_t tmem = *tmem_slot;
 
     if (warp == SNEVAL + 1) {
-        // ---------------- producer
+        // ---------------- producer: lane 0 issues the copies; the warp classifies the next
+        // 32 blocks at a time (one box test per lane, one ballot), so no per-block load
+        // waits in front of a copy
+        const uint32_t xb = (uint32_t)(BR * dd * 4);
+        const uint32_t bb = (uint32_t)L.b_bytes;
+        float blo[8], bhi[8];  // this CTA's tile box
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            blo[a] = a < dd ? p.tbox[(size_t)I * 2 * dd + a] : 0.f;
+            bhi[a] = a < dd ? p.tbox[(size_t)I * 2 * dd + dd + a] : 0.f;
+        }
         if (lane == 0) {
-            const uint32_t xb = (uint32_t)(BR * dd * 4);
-            const uint32_t bb = (uint32_t)L.b_bytes;
             mbar_expect_tx(vfull, bb);
             bulk_g2s(vimg, p.img + (size_t)I * bb, bb, vfull);
-            int b = 0;
-            int J = I;
-            for (; b < T; ++b, J = (J + 1 == NB) ? 0 : J + 1) {
-                const int s = b % SL;
-                if (b >= SL && !mbar_wait(&empty[s], ((b / SL) - 1) & 1)) {
-                    atomicOr(s_err, ERR_TIMEOUT);
-                    break;
+        }
+        int b = 0;
+        int J = I;
+        bool stop = false;
+        for (int b0 = 0; b0 < T && !stop; b0 += 32) {
+            // far: the boxes of tiles I and Jl are at least sqrt(thr2) apart
+            bool f = false;
+            const int bl = b0 + lane;
+            if (p.far_on && bl < T) {
+                const int Jl = (I + bl) % NB;
+                float gap2 = 0.f;
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    if (a < dd) {
+                        const float lj = p.tbox[(size_t)Jl * 2 * dd + a], hj = p.tbox[(size_t)Jl * 2 * dd + dd + a];
+                        const float g = fmaxf(0.f, fmaxf(lj - bhi[a], blo[a] - hj));
+                        gap2 = fmaf(g, g, gap2);
+                    }
                 }
-                uint8_t *st = lbase + (size_t)s * L.l_bytes;
-                mbar_expect_tx(&full[s], xb + bb);
-                bulk_g2s(st, p.img + (size_t)J * bb, bb, &full[s]);
-                bulk_g2s(st + L.b_bytes, p.Xp + (size_t)J * BR * dd, xb, &full[s]);
+                f = gap2 >= p.thr2;
             }
-            for (int u = std::max(0, b - SL); u < b; ++u)
+            const uint32_t fm = __ballot_sync(0xffffffffu, f);
+            if (lane == 0) {
+                const int bend = min(T, b0 + 32);
+                for (; b < bend; ++b, J = (J + 1 == NB) ? 0 : J + 1) {
+                    const int s = b % SL;
+                    if (b >= SL && !mbar_wait(&empty[s], ((b / SL) - 1) & 1)) {
+                        atomicOr(s_err, ERR_TIMEOUT);
+                        stop = true;
+                        break;
+                    }
+                    uint8_t *st = lbase + (size_t)s * L.l_bytes;
+                    s_far[s] = (int)((fm >> (b - b0)) & 1u);
+                    mbar_expect_tx(&full[s], xb + bb);
+                    bulk_g2s(st, p.img + (size_t)J * bb, bb, &full[s]);
+                    bulk_g2s(st + L.b_bytes, p.Xp + (size_t)J * BR * dd, xb, &full[s]);
+                }
+            }
+            stop = __shfl_sync(0xffffffffu, stop ? 1 : 0, 0) != 0;
+        }
+        if (lane == 0) {
+            for (int u = b - SL > 0 ? b - SL : 0; u < b; ++u)
                 if (!mbar_wait(&full[u % SL], (u / SL) & 1)) atomicOr(s_err, ERR_TIMEOUT);
             if (!mbar_wait(vfull, 0)) atomicOr(s_err, ERR_TIMEOUT);
         }
@@ -222,6 +272,7 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
                     break;
                 }
                 tc_fence_after();
+                const bool lo = NPROD == 3 && !s_far[s];  // K_lo products (near blocks only)
                 // Descriptors advance by a constant per K-step (the start address field is
                 // address >> 4 and no step carries out of it), so they are formed once.
                 const uint32_t a0 = smem_u32(abase + (size_t)sa * L.a_bytes);
@@ -234,7 +285,7 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
                 for (int ks = 0; ks < BR / 16; ++ks) {
                     const uint64_t step = (uint64_t)(ks * (256 >> 4));
                     mma_f16(dt, dah + step, dbh + step, idesc_w, (first && ks == 0) ? 0u : 1u);
-                    if (NPROD == 3) mma_f16(dt + SN, dal + step, dbh + step, idesc, 1u);
+                    if (lo) mma_f16(dt + SN, dal + step, dbh + step, idesc, 1u);
                 }
                 if (b >= 1) {
                     // D'_J = K_IJ^T V_I: the same tile MN-major (rows j; lbo = 2048 along i,
@@ -247,7 +298,7 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
                         const uint64_t astep = (uint64_t)(ks * ((2 * CORE_SBO) >> 4));
                         const uint64_t bstep = (uint64_t)(ks * (256 >> 4));
                         mma_f16(tdt, dat + astep, dvi + bstep, idesc_wt, ks == 0 ? 0u : 1u);
-                        if (NPROD == 3) mma_f16(tdt + SN, dalt + astep, dvi + bstep, idesc_t, 1u);
+                        if (lo) mma_f16(tdt + SN, dalt + astep, dvi + bstep, idesc_t, 1u);
                     }
                     mma_commit(&tfull[b & 1]);
                 }
@@ -349,14 +400,14 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
             mbar_arrive(&tempty[bb & 1]);
             int J = I + bb;
             if (J >= NB) J -= NB;
-            const int64_t r0 = (int64_t)J * BR;
-            if (r0 + row < p.n && !err_seen) {
+            const int64_t gj = (int64_t)J * BR + row;  // W row in tile order
+            if (gj < p.n && !err_seen) {
                 float val[CPT];
 #pragma unroll
                 for (int q = 0; q < CPT; ++q)
                     val[q] = (NPROD == 3 ? __uint_as_float(tr[q]) + __uint_as_float(tl[q]) : __uint_as_float(tr[q])) *
                              cscale_of(q);
-                add_row(r0 + row, val);
+                add_row(gj, val);
             }
         };
 
@@ -386,29 +437,35 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
                     xj[a][3] = make_float2(hi4.z, hi4.w);
                 }
             }
+            // near block: hi/lo split; far block: one fp16 rounding.  The choice is uniform
+            // over the block, so each form is compiled on its own (no predicated double work).
+            auto eval_tile = [&](auto split_tag) {
+                constexpr bool SPLIT = decltype(split_tag)::value;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                uint32_t w[4], l[4];
+                for (int k = 0; k < 4; ++k) {
+                    uint32_t w[4], l[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float2 u = make_float2(0.f, 0.f);
+                    for (int q = 0; q < 4; ++q) {
+                        float2 u = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int a = 0; a < 8; ++a) {
-                        if (a < dd) {
-                            const float2 dv = __fadd2_rn(xj[a][q], xr[k][a]);
-                            u = __ffma2_rn(dv, dv, u);
+                        for (int a = 0; a < 8; ++a) {
+                            if (a < dd) {
+                                const float2 dv = __fadd2_rn(xj[a][q], xr[k][a]);
+                                u = __ffma2_rn(dv, dv, u);
+                            }
                         }
+                        const float2 f = kval2<KIND>(u);
+                        if (SPLIT) split_f16(f, w[q], l[q]);
+                        else w[q] = pack2<BF16>(f.x, f.y);
                     }
-                    const float2 f = kval2<KIND>(u);
-                    if (NPROD == 3) split_f16(f, w[q], l[q]);
-                    else w[q] = pack2<BF16>(f.x, f.y);
+                    const int r = rg + 32 * k;
+                    const size_t off = (size_t)(r >> 3) * CORE_SBO + (size_t)kq * 128 + (size_t)(r & 7) * 16;
+                    *reinterpret_cast<uint4 *>(ast + off) = make_uint4(w[0], w[1], w[2], w[3]);
+                    if (SPLIT) *reinterpret_cast<uint4 *>(ast + HALF_TILE + off) = make_uint4(l[0], l[1], l[2], l[3]);
                 }
-                const int r = rg + 32 * k;
-                const size_t off = (size_t)(r >> 3) * CORE_SBO + (size_t)kq * 128 + (size_t)(r & 7) * 16;
-                *reinterpret_cast<uint4 *>(ast + off) = make_uint4(w[0], w[1], w[2], w[3]);
-                if (NPROD == 3)
-                    *reinterpret_cast<uint4 *>(ast + HALF_TILE + off) = make_uint4(l[0], l[1], l[2], l[3]);
-            }
+            };
+            if (NPROD == 3 && !s_far[s]) eval_tile(std::true_type{});
+            else eval_tile(std::false_type{});
             fence_async_smem();
             // D' buffer (b - 2) & 1 is released before this tile's MMA needs it
             if (ASYNC_T && b >= 3) drain_t_finish(b - 2);
@@ -438,15 +495,12 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) v[q] = __uint_as_float(h[q]);
             }
-            const int64_t r0 = (int64_t)I * BR;
-            if (r0 + row < p.n && !err_seen && !*reinterpret_cast<volatile int *>(s_err)) {
+            const int64_t gi = (int64_t)I * BR + row;  // W row in tile order
+            if (gi < p.n && !err_seen && !*reinterpret_cast<volatile int *>(s_err)) {
                 float outv[CPT];
 #pragma unroll
-                for (int q = 0; q < CPT; ++q) {
-                    const int col = c0 + q;
-                    outv[q] = col < p.c ? v[q] * cscale_of(q) + p.noise * p.V[(r0 + row) * p.c + col] : 0.f;
-                }
-                add_row(r0 + row, outv);
+                for (int q = 0; q < CPT; ++q) outv[q] = c0 + q < p.c ? v[q] * cscale_of(q) : 0.f;
+                add_row(gi, outv);
             }
         }
     }
@@ -460,9 +514,10 @@ __global__ void __launch_bounds__(SNTHREADS, 1) kz_sym_kernel(SymParams p, SymLa
     if (threadIdx.x == 0 && *s_err) atomicOr(p.err, *s_err);
 }
 
-// 128-point tiles, coordinate-major, log2 e folded in, far padding (as point_tiles_kernel)
-__global__ void sym_point_tiles_kernel(const float *Xs, int64_t n, int d, float factor, int64_t ntiles,
-                                       float *Xp) {
+// 128-point tiles of the points in the order perm, coordinate-major, log2 e folded in,
+// far padding
+__global__ void sym_point_tiles_kernel(const float *Xs, const int *perm, int64_t n, int d, float factor,
+                                       int64_t ntiles, float *Xp) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t per = (int64_t)BR * d;
     if (idx >= per * ntiles) return;
@@ -470,14 +525,32 @@ __global__ void sym_point_tiles_kernel(const float *Xs, int64_t n, int d, float 
     const int rem = (int)(idx % per);
     const int a = rem / BR, jj = rem % BR;
     const int64_t i = t * BR + jj;
-    Xp[idx] = i < n ? Xs[i * d + a] * factor : PAD_COORD;
+    const int64_t g = i < n ? (int64_t)perm[i] : -1;  // guarded: a position maps to a point < n
+    Xp[idx] = (g >= 0 && g < n) ? Xs[g * d + a] * factor : PAD_COORD;
+}
+
+// Box of each tile's real points (kernel units): tbox[t] = d minima, then d maxima.
+__global__ void sym_tile_box_kernel(const float *Xp, int64_t n, int d, int64_t ntiles, float *tbox) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= ntiles * d) return;
+    const int64_t t = idx / d;
+    const int a = (int)(idx % d);
+    const int cnt = (int)min((int64_t)BR, n - t * BR);
+    const float *x = Xp + t * BR * d + (int64_t)a * BR;
+    float lo = x[0], hi = x[0];
+    for (int jj = 1; jj < cnt; ++jj) {
+        lo = fminf(lo, x[jj]);
+        hi = fmaxf(hi, x[jj]);
+    }
+    tbox[t * 2 * d + a] = lo;
+    tbox[t * 2 * d + d + a] = hi;
 }
 
 // V operand image per 128-point tile: SN columns x 128 K values, canonical K-major
 // (byte offset (col/8)*2048 + (jj/8)*128 + (col%8)*16 + (jj%8)*2), hi then lo.
 template <bool BF16, int NPROD>
-__global__ void sym_image_kernel(const float *V, int64_t n, int c, int sn, int ntiles, const float *scale,
-                                 uint8_t *img) {
+__global__ void sym_image_kernel(const float *V, const int *perm, int64_t n, int c, int sn, int ntiles,
+                                 const float *scale, uint8_t *img) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t per_tile = (int64_t)sn * (BR / 8);
     if (idx >= per_tile * ntiles) return;
@@ -492,7 +565,8 @@ __global__ void sym_image_kernel(const float *V, int64_t n, int c, int sn, int n
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int64_t j = t * BR + kq * 8 + q;
-        v[q] = (j < n && col < c) ? V[j * c + col] * s : 0.f;
+        const int64_t g = j < n ? (int64_t)perm[j] : -1;
+        v[q] = (g >= 0 && g < n && col < c) ? V[g * c + col] * s : 0.f;
     }
     uint4 hi;
     hi.x = pack2<BF16>(v[0], v[1]); hi.y = pack2<BF16>(v[2], v[3]);
@@ -538,6 +612,19 @@ __global__ void sym_colscale_kernel(const float *part, int nb, int sn, float *sc
     colinv[col] = 1.0f / s;
 }
 
+// W[perm[r]] = Wt[r] + noise V[perm[r]]: the product back in the caller's point order,
+// with the diagonal noise term (every row written once: perm is a permutation)
+__global__ void sym_unpermute_kernel(const float *Wt, const int *perm, const float *V, int64_t n, int c, float noise,
+                                     float *W) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * c) return;
+    const int64_t r = idx / c;
+    const int col = (int)(idx - r * c);
+    const int64_t g = perm[r];
+    if (g < 0 || g >= n) return;
+    W[g * c + col] = Wt[idx] + noise * V[g * c + col];
+}
+
 template <int KIND, int DC, int NPROD, bool BF16, int SN>
 int launch_sym(const SymParams &p, const SymLayout &L, cudaStream_t st) {
     auto fn = kz_sym_kernel<KIND, DC, NPROD, BF16, SN>;
@@ -579,6 +666,22 @@ int launch_sym_all(int kind, int nprod, bool bf16, const SymParams &p, const Sym
 
 int sym_width(int c) { return c <= 16 ? 16 : SN_MAX; }
 
+// Squared distance (kernel units) beyond which a unit-variance kernel value is <= 2^-10,
+// so that one fp16 rounding (relative 2^-11) errs by at most 2^-21, as the hi/lo split of
+// a value near 1 does.  Matern: coordinates carry sqrt(5)/l log2 e, k(u) = (1 + u + u^2/3)
+// e^-u is decreasing; RBF: coordinates carry sqrt(log2 e)/(l sqrt 2), k = 2^-u2'.
+float far_threshold2(int kind) {
+    const double tau = 1.0 / 1024.0;
+    if (kind == LD_RBF) return (float)std::log2(1.0 / tau);
+    double lo = 0.0, hi = 100.0;
+    for (int it = 0; it < 200; ++it) {
+        const double u = 0.5 * (lo + hi);
+        ((1.0 + u + u * u / 3.0) * std::exp(-u) > tau ? lo : hi) = u;
+    }
+    const double up = hi * 1.4426950408889634;  // in units carrying log2 e
+    return (float)(up * up);
+}
+
 }  // namespace
 
 bool kz_sym_eligible(int64_t n, int d, int c, int precision) {
@@ -592,12 +695,16 @@ size_t kz_sym_workspace(int64_t n, int d, int c, int precision) {
     const int sn = sym_width(c);
     Arena a;
     a.measuring = true;
+    a.take<int>((size_t)n);                       // point order
+    a.take<float>((size_t)n * c);                 // the product in tile order
+    a.take<float>((size_t)NB * 2 * d);            // tile boxes
     a.take<float>((size_t)NB * BR * d);
     a.take<uint8_t>((size_t)NB * (nprod == 3 ? 2 : 1) * sn * BR * 2);
     a.take<float>(sn);
     a.take<float>(sn);
     a.take<float>((size_t)256 * sn);
     a.take<int>(4);
+    a.take<char>(point_order_workspace(n, d));    // the sort's scratch (released after it)
     return a.off;
 }
 
@@ -608,6 +715,9 @@ int kz_sym(const float *Xs, int64_t n, int d, int kind, double variance, double 
     const bool bf16 = precision == LD_BF16_TC;
     const int sn = sym_width(c);
     const size_t mark = ws.off;
+    int *perm = ws.take<int>((size_t)n);
+    float *Wt = ws.take<float>((size_t)n * c);
+    float *tbox = ws.take<float>((size_t)NB * 2 * d);
     float *Xp = ws.take<float>((size_t)NB * BR * d);
     uint8_t *img = ws.take<uint8_t>((size_t)NB * (nprod == 3 ? 2 : 1) * sn * BR * 2);
     float *scale = ws.take<float>(sn);
@@ -622,23 +732,28 @@ int kz_sym(const float *Xs, int64_t n, int d, int kind, double variance, double 
     int code = [&]() -> int {
         const float factor = kind == LD_RBF ? 1.2011224087864498f : 1.4426950408889634f;
         const int64_t cnt = NB * BR * d;
-        sym_point_tiles_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(Xs, n, d, factor, NB, Xp);
+        LD_TRY(point_order(Xs, n, d, perm, ws, st));  // tiles of spatially close points
+        sym_point_tiles_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(Xs, perm, n, d, factor, NB, Xp);
+        sym_tile_box_kernel<<<(unsigned)((NB * d + 255) / 256), 256, 0, st>>>(Xp, n, d, NB, tbox);
+        LD_TRY(check_launch("kz_sym tiles", 2));
         sym_colmax_kernel<<<256, 64, 0, st>>>(V, n, c, sn, part);
         sym_colscale_kernel<<<1, 64, 0, st>>>(part, 256, sn, scale, colinv);
         const int64_t nthr = NB * sn * (BR / 8);
         const unsigned gb = (unsigned)((nthr + 255) / 256);
-        if (bf16) sym_image_kernel<true, 1><<<gb, 256, 0, st>>>(V, n, c, sn, (int)NB, scale, img);
-        else if (nprod == 3) sym_image_kernel<false, 3><<<gb, 256, 0, st>>>(V, n, c, sn, (int)NB, scale, img);
-        else sym_image_kernel<false, 1><<<gb, 256, 0, st>>>(V, n, c, sn, (int)NB, scale, img);
-        LD_TRY(check_launch("kz_sym prep", 4));
-        LD_CHECK_CUDA(cudaMemsetAsync(W, 0, sizeof(float) * (size_t)n * c, st));
+        if (bf16) sym_image_kernel<true, 1><<<gb, 256, 0, st>>>(V, perm, n, c, sn, (int)NB, scale, img);
+        else if (nprod == 3) sym_image_kernel<false, 3><<<gb, 256, 0, st>>>(V, perm, n, c, sn, (int)NB, scale, img);
+        else sym_image_kernel<false, 1><<<gb, 256, 0, st>>>(V, perm, n, c, sn, (int)NB, scale, img);
+        LD_TRY(check_launch("kz_sym prep", 3));
+        LD_CHECK_CUDA(cudaMemsetAsync(Wt, 0, sizeof(float) * (size_t)n * c, st));
         LD_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
         SymParams p;
+        p.tbox = tbox;
+        p.thr2 = far_threshold2(kind);
+        p.far_on = nprod == 3 ? 1 : 0;
         p.Xp = Xp;
         p.img = img;
-        p.V = V;
         p.colinv = colinv;
-        p.W = W;
+        p.W = Wt;
         p.n = n;
         p.d = d;
         p.c = c;
@@ -646,13 +761,15 @@ int kz_sym(const float *Xs, int64_t n, int d, int kind, double variance, double 
         // D (x2 when drained, 2 SN wide with the hi/lo split) + two D'
         const int tcols = nprod == 3 ? 8 * sn : 3 * sn;
         p.ncols_tmem = tcols <= 32 ? 32 : (tcols <= 64 ? 64 : (tcols <= 128 ? 128 : (tcols <= 256 ? 256 : 512)));
-        p.vec_ok = (reinterpret_cast<uintptr_t>(W) % 16 == 0) && ((c * 4) % 16 == 0);
+        p.vec_ok = (reinterpret_cast<uintptr_t>(Wt) % 16 == 0) && ((c * 4) % 16 == 0);
         p.variance = (float)variance * KSCALE_INV;  // kernel values carry KSCALE
-        p.noise = (float)noise;
         p.err = err;
         const SymLayout L = make_sym_layout(sn, d, nprod, sym_stages(sn, d, nprod));
         if (sn == 16) LD_TRY(launch_sym_all<16>(kind, nprod, bf16, p, L, st));
         else LD_TRY(launch_sym_all<SN_MAX>(kind, nprod, bf16, p, L, st));
+        const int64_t tot = n * c;
+        sym_unpermute_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Wt, perm, V, n, c, (float)noise, W);
+        LD_TRY(check_launch("kz_sym unpermute"));
         int herr = 0;
         LD_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
         LD_CHECK_CUDA(cudaStreamSynchronize(st));
