@@ -160,6 +160,11 @@ size_t kz_tc_workspace(int64_t n, int d, int c, int precision);
 // W = M V on the tensor cores for a stored dense M (row-major n x n float32, positive
 // semidefinite: it is scaled by a power of two taken from its diagonal), kz_tc.cu
 size_t dense_tc_workspace(int64_t n, int c, int precision);
+// Stored-M product fed by tensor copies (dense_tma.cu): columns c0 .. c0 + N - 1 of
+// W = M V from the operand image and column scales dense_tc prepared.
+bool dense_tma_eligible(const float *M, int64_t n, int N, int precision);
+int dense_tma(const float *M, int64_t n, const uint8_t *img, const float *colinv, const float *mscale, float *W,
+              int c, int c0, int N, int precision, int *err, cudaStream_t st);
 int dense_tc(const float *M, int64_t n, const float *V, float *W, int c, int precision, Arena &ws,
              cudaStream_t st);
 // symmetric tensor-core product for c <= 16 (each kernel value evaluated once)

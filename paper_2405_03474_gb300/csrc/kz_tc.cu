@@ -802,6 +802,10 @@ int dense_tc(const float *M, int64_t n, const float *V, float *W, int c, int pre
         for (int c0 = 0; c0 < c; c0 += MAX_N) {
             const int N = chunk_N(std::min(MAX_N, c - c0));
             LD_TRY(prep_chunk(V, n, c, c0, N, ntiles, nprod, bf16, part, scale, colinv, img, st));
+            if (dense_tma_eligible(M, n, N, precision)) {  // M streamed by tensor copies
+                LD_TRY(dense_tma(M, n, img, colinv, mscale, W, c, c0, N, precision, err, st));
+                continue;
+            }
             TcParams p;
             p.Xp = nullptr;
             p.img = img;

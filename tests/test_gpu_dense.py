@@ -66,11 +66,16 @@ TC_TOL = {"f16_tc": 2.0 ** -9, "bf16_tc": 2.0 ** -6, "f16x3_tc": 2.0 ** -16}
 
 @pytest.mark.parametrize("prec", ["f16x3_tc", "f16_tc", "bf16_tc"])
 @pytest.mark.parametrize("n,c,variance", [(1000, 16, 1.3), (777, 5, 1.3), (2049, 64, 0.7), (300, 300, 1.0),
-                                          (128, 1, 1.0), (640, 130, 2.5), (1500, 24, 1e-3)])
+                                          (128, 1, 1.0), (640, 130, 2.5), (1500, 24, 1e-3), (1100, 64, 1.0),
+                                          (2052, 96, 0.9), (4100, 128, 1.1), (516, 48, 1.0)])
 def test_dense_tensor_core_product_matches_oracle(prec, n, c, variance):
-    # n % 4 == 0 reads M with 16-byte loads, otherwise per element; 300 columns run two
-    # 256-column chunks; 130 columns (N = 144) accumulate hi/lo without drains; a
-    # variance of 1e-3 checks the power-of-two scale taken from the diagonal
+    # n % 4 == 0 with n >= 128 and at most 128 columns streams M by tensor copies (the
+    # last tile of n = 1100 has a second box wholly past column n, n = 2052 leaves 4
+    # columns in its last tile, 4100 rows end 4 into a row block; 96 and 128 columns
+    # use the 512-column accumulator and two stages with the hi/lo split); other n read
+    # M per thread (n % 4 != 0 per element); 300 columns run two 256-column chunks; 130
+    # columns (N = 144) accumulate hi/lo without drains; a variance of 1e-3 checks the
+    # power-of-two scale taken from the diagonal
     kind = api.MATERN52 if n % 2 else api.RBF
     X = inputs.points(n, 3, "normal", seed=5)
     k = api.Kernel(kind, 0.4, variance, 1e-2 * variance)
