@@ -46,33 +46,38 @@ struct DenseParams {
     const uint8_t *img;   // operand image of V: per tile, nprod x (N x 64) halves, canonical K-major
     const float *colinv;  // 1 / column scale (N)
     const float *mscale;  // [0] power-of-two scale of M, [1] its inverse
-    float *W;             // n x c, columns c0 .. c0 + N - 1 written
+    float *W;             // n x c, columns c0 .. c0 + N - 1 written (added to, when split)
     int64_t n;
     int c, c0, N, ntiles, ncols_tmem;
+    int split;            // CTAs per 128-row block, each over a contiguous range of the j tiles
     int *err;
 };
 
+// M stages (released by the eval warps once read), V image stages (released by the
+// MMAs), two fp16 operand tiles
 struct DenseLayout {
-    int sl, b_bytes, stage_bytes, a_bytes, st_off, a_off, total;
+    int sm, sv, b_bytes, vstage_bytes, a_bytes, m_off, v_off, a_off, total;
 };
 
 inline int round1k(int b) { return ((b + 1023) / 1024) * 1024; }
 
-DenseLayout make_dense_layout(int N, int nprod, int sl) {
+DenseLayout make_dense_layout(int N, int nprod, int sm) {
     DenseLayout L;
-    L.sl = sl;
+    L.sm = sm;
+    L.sv = 2;
     L.b_bytes = (nprod == 3 ? 2 : 1) * N * DJ * 2;
-    L.stage_bytes = DM_TILE + round1k(L.b_bytes);  // M tile first (1024-aligned for the swizzle)
+    L.vstage_bytes = round1k(L.b_bytes);
     L.a_bytes = (nprod == 3 ? 2 : 1) * DA_HALF;
-    L.st_off = 1024;
-    L.a_off = L.st_off + sl * L.stage_bytes;
+    L.m_off = 1024;  // 1024-aligned for the 128-byte swizzle
+    L.v_off = L.m_off + sm * DM_TILE;
+    L.a_off = L.v_off + L.sv * L.vstage_bytes;
     L.total = L.a_off + 2 * L.a_bytes + 1024;  // + alignment slack of the dynamic base
     return L;
 }
 
 int dense_stages(int N, int nprod) {
-    for (int s = 4; s >= 2; --s)
-        if (make_dense_layout(N, nprod, s).total <= 225 * 1024) return s;
+    for (int s = 6; s >= 2; --s)
+        if (make_dense_layout(N, nprod, s).total <= 226 * 1024) return s;
     return 0;
 }
 
@@ -101,31 +106,41 @@ __global__ void __launch_bounds__(DTHREADS, 1)
     constexpr bool DRAIN = NPROD == 3;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);  // [sl] M tile and V image landed
-    uint64_t *empty = full + 8;                           // [sl] MMAs done with the stage
-    uint64_t *afull = empty + 8;                          // [2] fp16 tile written
+    uint64_t *mfull = reinterpret_cast<uint64_t *>(smem);  // [sm] M tile landed
+    uint64_t *mempty = mfull + 8;                          // [sm] eval warps done reading it
+    uint64_t *vfull = mempty + 8;                          // [2] V image landed
+    uint64_t *vempty = vfull + 2;                          // [2] MMAs done with it
+    uint64_t *afull = vempty + 2;                          // [2] fp16 tile written
     uint64_t *aempty = afull + 2;                         // [2] MMAs done with the fp16 tile
     uint64_t *done = aempty + 2;                          // every MMA done
     uint64_t *cfull = done + 1;                           // [2] chunk accumulated in TMEM
     uint64_t *cempty = cfull + 2;                         // [2] chunk drained
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cempty + 2);
     int *s_err = reinterpret_cast<int *>(tmem_slot + 1);
-    uint8_t *stbase = smem + L.st_off;
+    uint8_t *mbase = smem + L.m_off;
+    uint8_t *vbase = smem + L.v_off;
     uint8_t *abase = smem + L.a_off;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int row0 = blockIdx.x * DM;
-    const int T = p.ntiles;
-    const int SL = L.sl;
+    // this CTA: rows row0 .. row0 + 127, tiles t0 .. t0 + T - 1 (local index tl = t - t0)
+    const int row0 = (blockIdx.x / p.split) * DM;
+    const int part = blockIdx.x % p.split;
+    const int t0 = (int)((int64_t)p.ntiles * part / p.split);
+    const int T = (int)((int64_t)p.ntiles * (part + 1) / p.split) - t0;
+    const int SM_ = L.sm, SV = L.sv;
     const int N = p.N;
     // accumulator columns: [K_hi V_hi | K_hi V_lo + K_lo V_hi] with the split, else N
     const uint32_t NW = NPROD == 3 ? 2u * (uint32_t)N : (uint32_t)N;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < SL; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+        for (int s = 0; s < SM_; ++s) {
+            mbar_init(&mfull[s], 1);
+            mbar_init(&mempty[s], DEVAL * 32);
+        }
+        for (int s = 0; s < SV; ++s) {
+            mbar_init(&vfull[s], 1);
+            mbar_init(&vempty[s], 1);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&afull[s], DEVAL * 32);
@@ -154,23 +169,33 @@ __global__ void __launch_bounds__(DTHREADS, 1)
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mmap)) : "memory");
             const uint32_t bb = (uint32_t)L.b_bytes;
-            int t = 0;
-            for (; t < T; ++t) {
-                const int s = t % SL;
-                if (t >= SL && !mbar_wait(&empty[s], ((t / SL) - 1) & 1)) {
+            int tm = 0, tv = 0;  // M tiles and V images whose copies were issued
+            for (int tl = 0; tl < T; ++tl) {
+                const int t = t0 + tl;
+                const int sm = tl % SM_, sv = tl % SV;
+                if (tl >= SM_ && !mbar_wait(&mempty[sm], ((tl / SM_) - 1) & 1)) {
                     atomicOr(s_err, ERR_TIMEOUT);
                     break;
                 }
-                uint8_t *st = stbase + (size_t)s * L.stage_bytes;
-                mbar_expect_tx(&full[s], (uint32_t)DM_TILE + bb);
+                uint8_t *mst = mbase + (size_t)sm * DM_TILE;
+                mbar_expect_tx(&mfull[sm], (uint32_t)DM_TILE);
                 // x = 64 t (+ 32): 128-byte aligned column offsets; rows or columns past n read as 0
-                tma_load_2d(st, &mmap, t * DJ, row0, &full[s]);
-                tma_load_2d(st + DM_TILE / 2, &mmap, t * DJ + DBOX, row0, &full[s]);
-                bulk_g2s(st + DM_TILE, p.img + (size_t)t * bb, bb, &full[s]);
+                tma_load_2d(mst, &mmap, t * DJ, row0, &mfull[sm]);
+                tma_load_2d(mst + DM_TILE / 2, &mmap, t * DJ + DBOX, row0, &mfull[sm]);
+                tm = tl + 1;
+                if (tl >= SV && !mbar_wait(&vempty[sv], ((tl / SV) - 1) & 1)) {
+                    atomicOr(s_err, ERR_TIMEOUT);
+                    break;
+                }
+                mbar_expect_tx(&vfull[sv], bb);
+                bulk_g2s(vbase + (size_t)sv * L.vstage_bytes, p.img + (size_t)t * bb, bb, &vfull[sv]);
+                tv = tl + 1;
             }
             // every issued copy lands before the CTA may exit
-            for (int u = std::max(0, t - SL); u < t; ++u)
-                if (!mbar_wait(&full[u % SL], (u / SL) & 1)) atomicOr(s_err, ERR_TIMEOUT);
+            for (int u = std::max(0, tm - SM_); u < tm; ++u)
+                if (!mbar_wait(&mfull[u % SM_], (u / SM_) & 1)) atomicOr(s_err, ERR_TIMEOUT);
+            for (int u = std::max(0, tv - SV); u < tv; ++u)
+                if (!mbar_wait(&vfull[u % SV], (u / SV) & 1)) atomicOr(s_err, ERR_TIMEOUT);
         }
     } else if (warp == DEVAL) {
         // ---------------- MMA issuer
@@ -179,7 +204,7 @@ __global__ void __launch_bounds__(DTHREADS, 1)
             const uint32_t idesc = make_idesc(DM, N, BF16 ? 1u : 0u);
             bool ok = true;
             for (int t = 0; t < T && ok; ++t) {
-                const int s = t % SL, sa = t & 1;
+                const int sv = t % SV, sa = t & 1;
                 const int k = t / DKCH;
                 const bool first = DRAIN ? (t % DKCH == 0) : (t == 0);
                 const uint32_t dt = tmem + (DRAIN ? (uint32_t)((k & 1) * NW) : 0u);
@@ -187,13 +212,13 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                     ok = false;
                     break;
                 }
-                if (!mbar_wait(&afull[sa], (t >> 1) & 1) || !mbar_wait(&full[s], (t / SL) & 1)) {
+                if (!mbar_wait(&afull[sa], (t >> 1) & 1) || !mbar_wait(&vfull[sv], (t / SV) & 1)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t a0 = smem_u32(abase + (size_t)sa * L.a_bytes);
-                const uint32_t b0 = smem_u32(stbase + (size_t)s * L.stage_bytes + DM_TILE);
+                const uint32_t b0 = smem_u32(vbase + (size_t)sv * L.vstage_bytes);
                 // A: K-major no swizzle (lbo = 128 along j, sbo = 1024 along rows); B likewise,
                 // rows of B = columns of V, the lo half's rows following the hi half's
                 const uint64_t dah = make_desc(a0, 128, 1024);
@@ -205,7 +230,7 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                     mma_f16(dt, dah + step, dbh + step, idesc_w, (first && ks == 0) ? 0u : 1u);
                     if (NPROD == 3) mma_f16(dt + (uint32_t)N, dal + step, dbh + step, idesc, 1u);
                 }
-                mma_commit(&empty[s]);
+                mma_commit(&vempty[sv]);
                 mma_commit(&aempty[sa]);
                 if (DRAIN && (t % DKCH == DKCH - 1 || t == T - 1)) mma_commit(&cfull[k & 1]);
             }
@@ -258,12 +283,12 @@ __global__ void __launch_bounds__(DTHREADS, 1)
         const int C = (T + DKCH - 1) / DKCH;
         int drained = 0;
         for (int t = 0; t < T; ++t) {
-            const int s = t % SL, sa = t & 1;
+            const int sm = t % SM_, sa = t & 1;
             err_seen = err_seen || *reinterpret_cast<volatile int *>(s_err) != 0;
             if (DRAIN && t % DKCH == DKCH / 2 && t >= DKCH + DKCH / 2) drain(drained++);
-            wait_ok(&full[s], (t / SL) & 1);
+            wait_ok(&mfull[sm], (t / SM_) & 1);
             if (t >= 2) wait_ok(&aempty[sa], ((t >> 1) - 1) & 1);
-            const uint8_t *mt = stbase + (size_t)s * L.stage_bytes;
+            const uint8_t *mt = mbase + (size_t)sm * DM_TILE;
             uint8_t *ast = abase + (size_t)sa * L.a_bytes;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -292,6 +317,7 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                     *reinterpret_cast<uint4 *>(ast + DA_HALF + off) = make_uint4(l[0], l[1], l[2], l[3]);
                 }
             }
+            mbar_arrive(&mempty[sm]);  // M stage read (values in registers, stored above)
             fence_async_smem();
             mbar_arrive(&afull[sa]);
         }
@@ -320,7 +346,13 @@ __global__ void __launch_bounds__(DTHREADS, 1)
 #pragma unroll
             for (int q = 0; q < NH; ++q) {
                 const int cc = half * nh + q;
-                if (q < nh && p.c0 + cc < p.c) p.W[i * p.c + p.c0 + cc] = acc[q] * post * p.colinv[cc];
+                if (q < nh && p.c0 + cc < p.c) {
+                    const float v = acc[q] * post * p.colinv[cc];
+                    // split row blocks: two partial sums added into a zeroed W (two fp32 adds
+                    // to 0 commute, so the result does not depend on their order)
+                    if (p.split > 1) atomicAdd(&p.W[i * p.c + p.c0 + cc], v);
+                    else p.W[i * p.c + p.c0 + cc] = v;
+                }
             }
         }
     }
@@ -419,7 +451,24 @@ int dense_tma(const float *M, int64_t n, const uint8_t *img, const float *colinv
     p.ncols_tmem = cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512)));
     p.err = err;
     const DenseLayout L = make_dense_layout(N, nprod, dense_stages(N, nprod));
-    const int nblocks = (int)((n + DM - 1) / DM);
+    // One CTA per SM: split each row block's tiles over two CTAs when that fills the last
+    // wave better (n = 65536: 512 row blocks are 3.4 waves on 152 SMs, 1024 halves 6.7)
+    const int rblocks = (int)((n + DM - 1) / DM);
+    int dev = 0, sms = 0;
+    LD_CHECK_CUDA(cudaGetDevice(&dev));
+    LD_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    auto fill = [&](int split) {
+        const int64_t units = (int64_t)rblocks * split;
+        const int64_t waves = (units + sms - 1) / sms;
+        return (double)units / (double)(waves * sms);
+    };
+    p.split = (p.ntiles >= 2 * DKCH && fill(2) > fill(1) + 0.02) ? 2 : 1;
+    if (p.split > 1) {
+        const int cols_here = std::min(N, c - c0);
+        LD_CHECK_CUDA(cudaMemset2DAsync(W + c0, (size_t)c * sizeof(float), 0, (size_t)cols_here * sizeof(float),
+                                        (size_t)n, st));
+    }
+    const int nblocks = rblocks * p.split;
     if (bf16) return launch_dense_tma_n<1, true>(map, p, L, nblocks, st);
     if (nprod == 3) return launch_dense_tma_n<3, false>(map, p, L, nblocks, st);
     return launch_dense_tma_n<1, false>(map, p, L, nblocks, st);

@@ -508,28 +508,34 @@ __global__ void colscale_kernel(const float *part, int nb, int N, float *scale, 
     colinv[col] = 1.0f / s;
 }
 
-// Scale of a stored M: the power of two s with max_i |M_ii| s in [KSCALE / 2, KSCALE)
-// (s = KSCALE when the diagonal is zero or not finite); for a positive semidefinite M
-// every entry satisfies |M_ij| <= max_i M_ii, so every scaled entry lies in
-// [-KSCALE, KSCALE], inside fp16's range with full precision down to ~1e-9 max M_ii
-// (as for the computed kernel values).
-__global__ void diag_scale_kernel(const float *M, int64_t n, float *mscale) {
+// max_i |M_ii| over many blocks: the bit patterns of non-negative floats order like the
+// floats, so an integer atomic max of them is the float max (NaN entries are skipped by
+// fmaxf, as in a serial scan).  mx must be zero before the launch.
+__global__ void diag_max_kernel(const float *M, int64_t n, unsigned *mx) {
     __shared__ float red[256];
     float m = 0.f;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(M[i * n + i]));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(M[i * n + i]));
     red[threadIdx.x] = m;
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
         if (threadIdx.x < h) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + h]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const float mx = red[0];
-        int e = 0;
-        if (mx > 0.f && isfinite(mx)) frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
-        mscale[0] = ldexpf(1.0f, KSCALE_LOG2 - e);
-        mscale[1] = ldexpf(1.0f, e - KSCALE_LOG2);
-    }
+    if (threadIdx.x == 0) atomicMax(mx, __float_as_uint(red[0]));
+}
+
+// Scale of a stored M: the power of two s with max_i |M_ii| s in [KSCALE / 2, KSCALE)
+// (s = KSCALE when the diagonal is zero or not finite); for a positive semidefinite M
+// every entry satisfies |M_ij| <= max_i M_ii, so every scaled entry lies in
+// [-KSCALE, KSCALE], inside fp16's range with full precision down to ~1e-9 max M_ii
+// (as for the computed kernel values).
+__global__ void diag_scale_kernel(const unsigned *mx, float *mscale) {
+    const float m = __uint_as_float(*mx);
+    int e = 0;
+    if (m > 0.f && isfinite(m)) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+    mscale[0] = ldexpf(1.0f, KSCALE_LOG2 - e);
+    mscale[1] = ldexpf(1.0f, e - KSCALE_LOG2);
 }
 
 // Operand image of V: per j-tile t, per product half (hi, lo), N rows (columns of V)
@@ -795,8 +801,11 @@ int dense_tc(const float *M, int64_t n, const float *V, float *W, int c, int pre
         return LD_ERR_WORKSPACE;
     }
     int code = [&]() -> int {
-        diag_scale_kernel<<<1, 256, 0, st>>>(M, n, mscale);
-        LD_TRY(check_launch("diag_scale"));
+        unsigned *mx = reinterpret_cast<unsigned *>(mscale + 2);
+        LD_CHECK_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned), st));
+        diag_max_kernel<<<(unsigned)std::min<int64_t>(1024, (n + 255) / 256), 256, 0, st>>>(M, n, mx);
+        diag_scale_kernel<<<1, 1, 0, st>>>(mx, mscale);
+        LD_TRY(check_launch("diag_scale", 2));
         LD_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
         const bool vec4 = n % 4 == 0 && reinterpret_cast<uintptr_t>(M) % 16 == 0;
         for (int c0 = 0; c0 < c; c0 += MAX_N) {
