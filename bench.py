@@ -46,8 +46,10 @@ ROWS_PER_CORE = 4
 # dram__bytes_write.sum, one pass, n = 2^20, 16 columns, hi/lo fp16: 1.04 GB read +
 # 0.74 GB written), valid only for the kernel sources it was taken on (first 16 hex
 # digits of their sha256); reported as null once those sources change.
-KZ_SYM_TRAFFIC = {"bytes": 1.04e9 + 0.74192e9, "sources": {"paper_2405_03474_gb300/csrc/kz_sym.cu": "b7baadfa39d6bc2d",
-                                                          "paper_2405_03474_gb300/csrc/tc_common.cuh": "9ab49c92642e95a3"}}
+KZ_SYM_TRAFFIC = {"bytes": 640137216 + 523443200,
+                  "sources": {"paper_2405_03474_gb300/csrc/kz_sym.cu": "a34863b4a563c595",
+                              "paper_2405_03474_gb300/csrc/point_order.cu": "4fec982c8b04b2a4",
+                              "paper_2405_03474_gb300/csrc/tc_common.cuh": "9ab49c92642e95a3"}}
 
 
 def measured_traffic(record):
@@ -449,8 +451,8 @@ def run_ours(args, rank, world, local_rank, pool):
         sym_roof["traffic"] = measured_traffic(KZ_SYM_TRAFFIC)
         sym_roof["traffic_note"] = ("DRAM bytes per launch from one ncu capture (n=2^20, 16 columns); the "
                                     "algorithmic DRAM bytes of a matrix-free launch are only its inputs and "
-                                    "output (X tiles, V image, W: ~0.2 GB); the rest is L2 spill of the V "
-                                    "image and W at this n")
+                                    "output (X tiles, V image, W in tile order: ~0.2 GB); the rest is L2 "
+                                    "spill of the V image and W at this n")
     roofs = [r for r in (sym_roof, roof("kz_wide_kernel"), roof("kz_tc_kernel")) if r]
     roofs.sort(key=lambda r: -r["share_of_step"])
     dominant, others = (roofs[0] if roofs else None), roofs[1:]
