@@ -17,7 +17,7 @@ import time
 import numpy as np
 import torch
 
-from . import api, inputs
+from . import _lib, api, inputs
 
 
 def features(theta, n):
@@ -48,12 +48,19 @@ class Estimator:
         self.sketch_precision = sketch_precision
 
     def __call__(self, theta):
+        """log det / n at theta, or NaN where the operator in the estimator's precision
+        is not positive definite (LD_ERR_NOT_SPD: the rounding of K exceeds the noise,
+        which happens at the box's long-lengthscale, low-noise corner)."""
         l, v, nu = (float(x) for x in theta)
         kern = api.Kernel(self.kind, l, v, nu)
         P = api.Precond.build(self.X, kern, self.rank, power_iters=self.power_iters, seed=inputs.SEED_SKETCH,
                               precision=self.sketch_precision)
         try:
             res = api.logdet_estimate(self.X, kern, precond=P, **self.opts)
+        except _lib.LogdetError as e:
+            if e.status != _lib.LD_ERR_NOT_SPD:
+                raise
+            return float("nan")
         finally:
             P.free()
         return res["logdet"] / self.n
@@ -127,9 +134,11 @@ def train_and_evaluate(est, thetas, labels, held_out=64, queries=65536, epochs=8
     """Fit on labels, then report what the network gains: error against fresh
     estimator values on held-out hyperparameters, time per query of batched
     inference against time per estimate, and an audit."""
+    thetas, labels = np.asarray(thetas), np.asarray(labels)
+    ok = np.isfinite(labels)  # settings where the estimator's operator was not positive definite carry NaN
     hs = HyperSurrogate(est, seed=seed)
     t0 = time.perf_counter()
-    loss = hs.fit(thetas, labels, epochs=epochs, batch=batch, lr=lr)
+    loss = hs.fit(thetas[ok], labels[ok], epochs=epochs, batch=batch, lr=lr)
     t_fit = time.perf_counter() - t0
     test = inputs.sobol_theta(held_out, seed=101)
     t0 = time.perf_counter()
@@ -143,12 +152,15 @@ def train_and_evaluate(est, thetas, labels, held_out=64, queries=65536, epochs=8
     hs.predict(q, want_grad=True)
     torch.cuda.synchronize()
     t_q = (time.perf_counter() - t0) / queries
-    err = np.abs(pred - ref)
-    return {"labels": int(len(labels)), "train_loss_normalised": loss, "fit_s": t_fit,
-            "held_out": held_out, "max_abs_err_logdet_per_n": float(err.max()),
+    fin = np.isfinite(ref)
+    err = np.abs(pred - ref)[fin]
+    ref = ref[fin]
+    return {"labels": int(len(labels)), "labels_not_spd": int((~ok).sum()), "train_loss_normalised": loss,
+            "fit_s": t_fit, "held_out": held_out, "held_out_not_spd": int((~fin).sum()),
+            "max_abs_err_logdet_per_n": float(err.max()),
             "mean_abs_err_logdet_per_n": float(err.mean()),
             "max_rel_err_logdet": float(np.max(err / np.abs(ref))),
-            "label_spread": float(np.max(labels) - np.min(labels)),
+            "label_spread": float(np.max(labels[ok]) - np.min(labels[ok])),
             "estimator_s_per_query": t_est, "surrogate_s_per_query_with_grad": t_q,
             "speedup_per_query": t_est / t_q, "queries": queries}
 
