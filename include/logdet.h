@@ -156,8 +156,11 @@ int ld_rk_coeffs(int32_t order, double *b, double *c, double *sigma);
  * precisions); anything else, empty inputs included, returns LD_ERR_INVALID
  * before any device work.  ws = NULL: the call allocates and frees its own
  * workspace.  Tensor-core dispatch (all within the call): c <= 48 and n >= 256
- * the symmetric product, 256 < c <= 512 in fp16/bf16 the one-pass wide
- * product, otherwise the general product in chunks of 256 columns. */
+ * the symmetric product (each 128 x 128 block evaluated once, the points taken
+ * in a Morton order of its own and blocks whose kernel values are all <= 2^-10
+ * of the variance rounded once to fp16 in LD_F16X3_TC), 256 < c <= 512 in
+ * fp16/bf16 the one-pass wide product, otherwise the general product in chunks
+ * of 256 columns. */
 size_t ld_kz_workspace_size(int64_t n, int32_t d, int32_t c, int32_t precision);
 int ld_kz(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
           const void *V_dev, void *W_dev, int32_t c, int32_t precision,
@@ -198,7 +201,10 @@ int ld_kz_dl(const double *X_dev, int64_t n, int32_t d, ld_kernel kern,
  * memory): M = K + noise I written row-major n-by-n (float64 for LD_FP64, float32
  * otherwise; ld_dense_bytes(n, precision) bytes, caller-owned), then W = M V
  * (V, W n-by-c row-major, float64 for LD_FP64, else float32) reading M once per
- * product.  LD_FP64 / LD_FP32: CUDA-core GEMM, asynchronous on the stream.
+ * pass over a chunk of columns.  LD_FP64 / LD_FP32: CUDA-core GEMM, asynchronous
+ * on the stream.  Tensor-core precisions: chunks of up to 256 columns; a chunk of
+ * at most 128 columns with n % 4 == 0, n >= 128 and M 16-byte aligned streams M
+ * into shared memory by TMA tensor copies, any other chunk by per-thread loads.
  * Tensor-core precisions (LD_BF16_TC, LD_F16_TC, LD_F16X3_TC; c <= 4096): M is
  * rounded (or split hi/lo) like the computed kernel values of ld_kz after
  * scaling by the power of two that brings max_i |M_ii| into [2^14, 2^15), so M
