@@ -24,4 +24,6 @@ def test_traffic_is_reported_only_for_the_sources_it_was_measured_on():
         digest = hashlib.sha256(f.read()).hexdigest()[:16]
     assert bench.measured_traffic({"bytes": 1.5e9, "sources": {rel: digest}}) == 1.5e9
     assert bench.measured_traffic({"bytes": 1.5e9, "sources": {rel: "0" * 16}}) is None
-    assert set(bench.KZ_SYM_TRAFFIC["sources"]) == {rel, "paper_2405_03474_gb300/csrc/tc_common.cuh"}
+    # the kernel, its device helpers, and the point order that decides which points share a tile
+    assert set(bench.KZ_SYM_TRAFFIC["sources"]) == {rel, "paper_2405_03474_gb300/csrc/tc_common.cuh",
+                                                    "paper_2405_03474_gb300/csrc/point_order.cu"}
