@@ -99,6 +99,14 @@ __device__ __forceinline__ void tmem_ld_x4(uint32_t taddr, uint32_t (&r)[4 * G])
                      : "r"(taddr + 4u * g));
 }
 
+// Completes the TMEM loads in flight; naming the destination registers keeps every use
+// of them after the wait.
+__device__ __forceinline__ void tmem_wait_regs(uint32_t (&a)[8], uint32_t (&b)[8]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) asm volatile("" : "+r"(a[q]), "+r"(b[q]));
+}
+
 // NH: columns per eval thread in drains and the epilogue (a half of N, at most 64)
 template <int NPROD, bool BF16, int NH>
 __global__ void __launch_bounds__(DTHREADS, 1)
@@ -272,7 +280,7 @@ __global__ void __launch_bounds__(DTHREADS, 1)
                     uint32_t h[8], l[8];
                     tmem_ld_x4<2>(ta + (uint32_t)c8, h);
                     tmem_ld_x4<2>(ta + (uint32_t)(N + c8), l);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    tmem_wait_regs(h, l);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) acc[c8 + q] += __uint_as_float(h[q]) + __uint_as_float(l[q]);
                 }
@@ -332,9 +340,9 @@ __global__ void __launch_bounds__(DTHREADS, 1)
 #pragma unroll
             for (int c8 = 0; c8 < NH; c8 += 8) {
                 if (c8 < nh) {
-                    uint32_t h[8];
+                    uint32_t h[8], unused[8] = {};
                     tmem_ld_x4<2>(ta + (uint32_t)c8, h);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    tmem_wait_regs(h, unused);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) acc[c8 + q] = __uint_as_float(h[q]);
                 }
