@@ -49,12 +49,18 @@ class Estimator:
 
     def __call__(self, theta):
         """log det / n at theta, or NaN where the operator in the estimator's precision
-        is not positive definite (LD_ERR_NOT_SPD: the rounding of K exceeds the noise,
-        which happens at the box's long-lengthscale, low-noise corner)."""
+        is not positive definite (LD_ERR_NOT_SPD from the preconditioner's Cholesky or
+        from the CG: the rounding of K exceeds the noise, which happens at the box's
+        long-lengthscale, low-noise corner)."""
         l, v, nu = (float(x) for x in theta)
         kern = api.Kernel(self.kind, l, v, nu)
-        P = api.Precond.build(self.X, kern, self.rank, power_iters=self.power_iters, seed=inputs.SEED_SKETCH,
-                              precision=self.sketch_precision)
+        try:
+            P = api.Precond.build(self.X, kern, self.rank, power_iters=self.power_iters, seed=inputs.SEED_SKETCH,
+                                  precision=self.sketch_precision)
+        except _lib.LogdetError as e:
+            if e.status != _lib.LD_ERR_NOT_SPD:
+                raise
+            return float("nan")
         try:
             res = api.logdet_estimate(self.X, kern, precond=P, **self.opts)
         except _lib.LogdetError as e:
