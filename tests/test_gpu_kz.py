@@ -221,3 +221,26 @@ def test_symmetric_product_repeats_against_oracle():
     ref, scale = M @ Vh, product_scale(M, Vh)
     for rep in range(15):
         assert_elementwise(host(api.ld_kz(X, V, k, "f16x3_tc")), ref, scale, TC_TOL["f16x3_tc"], "repeat %d" % rep)
+
+
+# Far blocks of the symmetric product: lengthscale 0.03 over 4133 points in [0,1]^2
+# makes 33 Morton-ordered 128-point tiles, most pairs of them far apart, and those
+# blocks are rounded once to fp16 instead of split hi/lo.  A far block holds only
+# entries <= 2^-10 of the variance, so the error is bounded by the hi/lo bound over
+# |M||V|, plus one fp16 rounding (2^-11 relative) of every entry that small, plus the
+# spacing of fp16 subnormals (2^-25 of the 2^15-scaled values) for the tiniest ones.
+@pytest.mark.parametrize("kind", [api.RBF, api.MATERN52])
+@pytest.mark.parametrize("c", [16, 48])
+def test_kz_symmetric_far_blocks_within_one_fp16_rounding(kind, c):
+    n, d, ell, v, nu = 4133, 2, 0.03, 1.1, 1e-2
+    X = inputs.points(n, d, "uniform", seed=41)
+    V = inputs.gaussian(n, c, seed=42)
+    W = host(api.ld_kz(cuda(X), cuda(V, torch.float32), api.Kernel(kind, ell, v, nu), "f16x3_tc"))
+    M = kernels.kernel_matrix(X, kind, ell, v, nu)
+    K = np.abs(M - nu * np.eye(n))
+    small = np.where(K <= v * 2.0 ** -10, K, 0.0)
+    assert (K <= v * 2.0 ** -10).mean() > 0.9  # most pairs are that small (94-96% here)
+    bound = (TC_TOL["f16x3_tc"] * product_scale(M, V) + 2.0 ** -11 * (small @ np.abs(V))
+             + 2.0 ** -40 * v * np.abs(V).sum(axis=0))
+    err = np.abs(W - M @ V)
+    assert np.all(err <= bound), float(np.max(err / bound))
