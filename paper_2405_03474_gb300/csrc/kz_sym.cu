@@ -15,9 +15,9 @@
 //     issued before the next tile's evaluation and completed after it) and add it
 //     into W_J, each thread one 16-byte vector reduction (red.global.add.v4.f32)
 //     of 4 columns of one row.
-// W is zeroed first and every contribution (including the owner's own rows and
-// the noise term, at the end) is added, so the order of additions across CTAs is
-// the only run-to-run difference (fp32 rounding).  D_I is accumulated in tensor
+// The product accumulates into a zeroed buffer in tile order; every contribution
+// (including the owner's own rows, at the end) is added, so the order of additions
+// across CTAs is the only run-to-run difference (fp32 rounding).  D_I is accumulated in tensor
 // memory in chunks of 4 blocks and drained to fp32 round-to-nearest partial
 // sums, held in registers (each eval thread owns a quarter of one row's columns),
 // as in the non-symmetric kernel.  The kernel is compiled for SN = 16 and SN = 48
@@ -27,8 +27,8 @@
 // and most pairs of tiles are far apart.  With the hi/lo split, a block whose tiles'
 // boxes are so far apart that every kernel value is <= 2^-10 (of the variance) is rounded
 // to fp16 once and its K_lo products are skipped: one rounding of such values errs by at
-// most 2^-21, no more than the split does near 1.  Rows of W and V are reached through
-// the permutation.
+// most 2^-21, no more than the split does near 1.  The tile-order product is scattered
+// back to the caller's order by one pass that also adds the noise term.
 #include <math.h>
 
 #include <algorithm>
