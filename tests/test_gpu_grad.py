@@ -1,6 +1,8 @@
 """Gradient of the estimator (hand-written adjoint) at the gradient workload's scales:
 parity with the oracle's frozen-P gradient and the exact FP64 gradient at n = 4096,
-central finite differences at n = 131072, and the torch.autograd.Function."""
+central finite differences of the FP64 estimate at n = 32768 and at the workload's
+n = 131072, the reduced precisions against FP64 at n = 131072, and the
+torch.autograd.Function."""
 import numpy as np
 import pytest
 
@@ -53,6 +55,12 @@ def _fd_check(n, prec, th, h_rel, rtol, rank=128, s=16):
 def test_grad_central_differences_fp64():
     # Differences of the converged fp64 estimate (P and probes frozen) against the adjoint.
     _fd_check(32768, "fp64", (0.2, 1.0, 1e-2), 1e-4, 1e-6)
+
+
+def test_grad_central_differences_fp64_n131072():
+    # The gradient workload's size (RBF, 2^17 points in [0,1]^2); theta = (0.2, 1, 0.1),
+    # where FP64 CG converges in tens of steps; 8 probes, P and probes frozen.
+    _fd_check(131072, "fp64", (0.2, 1.0, 0.1), 1e-4, 1e-5, rank=128, s=8)
 
 
 def _grads_n131072(th, precs, s=8):
